@@ -1,0 +1,329 @@
+"""Benchmark of the GB300 RTCUR hot path (one JSON line on stdout, rank 0).
+
+A step is one RTCUR iteration (Algorithm 1's loop body) on the 800^3 rank-5 workload: the
+sampled threshold + gather, the FP64 truncated pinv, the factor update, the sampled stopping
+error and, in the FULL scope (default), the dense fused threshold pass over the whole 2 GB
+tensor. `value` is iterations/s with X resident in HBM (X is 2.05 GB, larger than L2, so no
+flush is needed between iterations). Extra keys: the dense kernel's roofline (timed live with
+CUDA events on the stream it runs on), time to e <= 1e-5, an end-to-end number through the
+C ABI with host buffers, and the FP64 oracle timed on the host cores as the CPU baseline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--scope full|sampled] [--variant F|R] [--size D]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RTCUR iters/s & time-to-1e-5 at 800³ rank 5: BF16/TF32 vs FP32 plain, % HBM roofline"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scope", default="full", choices=["full", "sampled"])
+    ap.add_argument("--variant", default="F", choices=["F", "R"])
+    ap.add_argument("--size", type=int, default=800)
+    ap.add_argument("--rank", type=int, default=5)
+    ap.add_argument("--alpha", type=float, default=0.3)
+    ap.add_argument("--upsilon", type=float, default=3.0)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(a):
+    return (f"RTCUR-{a.variant} {a.scope.upper()} scope, {a.size}^3 FP32 Gaussian Tucker rank "
+            f"({a.rank},{a.rank},{a.rank}), {int(a.alpha * 100)}% outliers U[-10 mean|L*|, 10 mean|L*|], "
+            f"v={a.upsilon:g}, gamma=0.7, zeta0=max|X|, tol 1e-5")
+
+
+def make_problem(a):
+    from paper_2108_10448_gb300 import synth
+    p = synth.make_tucker_problem((a.size,) * 3, (a.rank,) * 3, a.alpha, a.upsilon, seed=a.seed,
+                                  keep_truth=False, max_iter=100)
+    n_sets = 100 if a.variant == "R" else 1
+    sets = synth.draw_index_sets(p.dims, p.m, p.q, seed=a.seed, n_sets=n_sets)
+    return p, sets
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def oracle_iteration_time(p, sets, a, budget_s=20.0):
+    """The FP64 oracle as it stands, timed on the host cores on a bounded sample of one
+    iteration: the full sampled step (gather, HT, Fiber CUR with LAPACK SVD, e^(k)) plus, in
+    the FULL scope, the dense threshold pass over a slab of mode-1 rows scaled to the tensor."""
+    from oracle import rtcur_oracle as O
+    X = p.X
+    Xd = X.astype(np.float64)  # setup, untimed (the oracle works in FP64)
+    st = O.RTCURState()
+    zeta = p.zeta0
+    ts = []
+    t_begin = time.perf_counter()
+    k = 0
+    while True:
+        zeta *= p.gamma
+        s = sets[0] if a.variant == "F" else sets[k % len(sets)]
+        t0 = time.perf_counter()
+        st, info = O.rtcur_step(Xd, st, s, zeta, p.ranks)
+        ts.append(time.perf_counter() - t0)
+        k += 1
+        if k >= 3 or time.perf_counter() - t_begin > budget_s * 0.6:
+            break
+    t_step = float(np.median(ts))
+    t_dense, rows_done = 0.0, 0
+    if a.scope == "full":
+        d0 = p.dims[0]
+        rows = max(1, min(d0, int(d0 * 0.05)))
+        t0 = time.perf_counter()
+        Lslab = O.tucker_full(st.core, [st.factors[0][:rows]] + list(st.factors[1:]))
+        Sslab = O.hard_threshold(X[:rows].astype(np.float64) - Lslab, zeta)
+        _ = float(np.sum((X[:rows] - Lslab - Sslab) ** 2))
+        t_dense = (time.perf_counter() - t0) * d0 / rows
+        rows_done = rows
+    return t_step + t_dense, {"t_sampled_step_s": t_step, "t_dense_pass_s": t_dense,
+                              "steps_timed": len(ts), "dense_rows_timed": rows_done}
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return
+    p, sets = make_problem(a)
+    K, W = a.steps, a.warmup
+    times = []
+    for _ in range(max(1, min(K, 3))):
+        t, det = oracle_iteration_time(p, sets, a)
+        times.append(t)
+    t = float(np.median(times))
+    value = 1.0 / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
+        "steps": K, "warmup": W, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(a)},
+        "cpu_baseline": {"value": value, "unit": "iters/s", "cores": cpu_cores(), "kind": "oracle",
+                         "sample": "median of bounded samples: one oracle iteration's sampled step "
+                                   "plus a 5% slab of the dense pass scaled to the tensor"},
+        "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(a, rank, world):
+    import torch
+    from paper_2108_10448_gb300 import rtcur as rt
+    from paper_2108_10448_gb300 import synth
+    import __graft_entry__ as ge
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0 or world == 1:
+        ge.build()
+    if world > 1:
+        torch.distributed.barrier()
+    rt.load()
+    p, sets = make_problem(a)
+    idx = synth.pack_index_sets(sets)
+    X = torch.from_numpy(p.X).to(dev)
+    L = torch.empty_like(X)
+    S = torch.empty_like(X)
+    scope = rt.SCOPE_FULL if a.scope == "full" else rt.SCOPE_SAMPLED
+    variant = rt.VARIANT_R if a.variant == "R" else rt.VARIANT_F
+    max_iter = 100
+    plan = rt.rtcur_create(p.dims, p.ranks, p.m, p.q, p.zeta0, p.gamma, p.tol, max_iter, variant,
+                           rt.make_options(scope=scope))
+    stream = torch.cuda.Stream(device=dev)
+    sh = stream.cuda_stream
+    K, W = a.steps, a.warmup
+    # --- iterations/s: W warm-up iterations, then K timed, device-timed with events ---
+    rt.rtcur_begin(plan, X.data_ptr(), idx, S.data_ptr(), sh)
+    rt.rtcur_iterate(plan, W, sh)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        rt.rtcur_iterate(plan, K, sh)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        torch.distributed.barrier()
+    res_it = rt.rtcur_finish(plan, 0, 0, sh, max_iter=max_iter)
+    value = world * K / (ms / 1e3)
+    # --- dominant kernel alone: the dense fused pass, same launch configuration ---
+    roof = None
+    if scope == rt.SCOPE_FULL:
+        rt.rtcur_threshold_dense(plan, 3, sh)
+        torch.cuda.synchronize()
+        nl = 10
+        ev0.record(stream)
+        rt.rtcur_threshold_dense(plan, nl, sh)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        dms = ev0.elapsed_time(ev1) / nl
+        N = int(np.prod(p.dims))
+        alg_bytes = 8.0 * N  # 4 B read of X + 4 B write of S per element
+        peak, src = peaks()
+        achieved = alg_bytes / (dms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "k_dense_fp32",
+                "ms_per_launch": dms, "peak_source": f"{src} (burst copy bandwidth)",
+                "algorithmic_bytes_per_launch": alg_bytes}
+    # --- time to tolerance: whole solve from X resident, one graph launch ---
+    ev0.record(stream)
+    res = rt.rtcur_solve(plan, X.data_ptr(), idx, L.data_ptr(), S.data_ptr(), sh, max_iter=max_iter)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ttt_ms = ev0.elapsed_time(ev1)
+    # --- end to end through the C ABI from pinned host buffers ---
+    Xh = torch.from_numpy(p.X).pin_memory()
+    Lh = torch.empty_like(Xh).pin_memory()
+    Xd = torch.empty_like(X)
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        Xd.copy_(Xh, non_blocking=True)
+        res_e2e = rt.rtcur_solve(plan, Xd.data_ptr(), idx, L.data_ptr(), 0, sh, max_iter=max_iter)
+        Lh.copy_(L, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_val = world * res_e2e.iters / e2e_s
+    rt.rtcur_destroy(plan)
+    if rank != 0:
+        return
+    n_modes = 3
+    launches_per_iter = (1 if scope == rt.SCOPE_FULL else 0) + 1 + 1 + 1 + 1 + 2 + n_modes + 2 + 1 + 1
+    line = {
+        "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_name(a), "dims": list(p.dims), "ranks": list(p.ranks),
+                   "nI": p.m, "nJ": p.q, "variant": a.variant, "scope": a.scope,
+                   "dense_form": "fp32 fused (FMA last-mode product)", "pinv": "fp64",
+                   "l2": "inputs larger than L2 (X is 2.05 GB), no flush",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "time_to_tol": {"ms": ttt_ms, "iters": res.iters, "e": res.e, "status": res.status,
+                        "includes": "index upload, max|X|, the graph-driven loop, L and S output"},
+        "e2e": {"value": e2e_val, "unit": "iters/s", "seconds": e2e_s, "iters": res_e2e.iters,
+                "h2d_bytes_per_step": int(p.X.nbytes), "d2h_bytes_per_step": int(p.X.nbytes),
+                "step": "one whole solve: H2D X, rtcur_solve to 1e-5, D2H L"},
+        "roofline": roof,
+        "gpu_launches": launches_per_iter * K,
+        "clocks": clk.summary(),
+    }
+    if not a.no_cpu_baseline:
+        t_or, det = oracle_iteration_time(p, sets, a)
+        line["cpu_baseline"] = {"value": 1.0 / t_or, "unit": "iters/s", "cores": cpu_cores(),
+                                "kind": "oracle",
+                                "sample": "one oracle iteration's sampled step (median of up to 3) "
+                                          "plus a 5% slab of the dense pass scaled to the tensor",
+                                **det}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        import torch
+        backend = "nccl" if a.impl == "ours" else "gloo"
+        torch.distributed.init_process_group(backend)
+    try:
+        if a.impl == "reference":
+            run_reference(a, rank, world)
+        else:
+            run_ours(a, rank, world)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

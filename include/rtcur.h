@@ -1,0 +1,170 @@
+/*
+ * rtcur.h -- C ABI of librtcur.so, the GB300 (sm_103a) hot path of RTCUR (Robust Tensor CUR),
+ * the alternating-projection robust tensor PCA method of Cai, Chao, Huang and Needell
+ * ("Fast Robust Tensor Principal Component Analysis via Fiber CUR Decomposition").
+ *
+ * The method (Algorithm 1) splits an observed tensor X = L + S into a low-multilinear-rank L
+ * and a sparse S. Each iteration k -> k+1:
+ *   zeta^(k+1) = gamma * zeta^(k)                                   (Sec. 3.2, decay)
+ *   S^(k+1)    = HT_{zeta^(k+1)}(X - L^(k)) on the sampled entries  (Eq. partial S update;
+ *                over the whole tensor too in the FULL scope, Eq. S=HT(X-L))
+ *   R = (X - S)(I_1..I_n),  C_i = (X - S)_(i)(:, J_i),  U_i = SVD_{r_i}(C_i(I_i, :))
+ *   L^(k+1)    = R x_1 (C_1 U_1^+) x_2 ... x_n (C_n U_n^+)           (Eq. L=CUR)
+ *   e^(k+1)    = sampled relative error                             (Eq. rel_err)
+ * until e^(k) <= tol or k = max_iter.
+ *
+ * Conventions for every entry point:
+ *   - Tensors are dense, row-major (C order, last mode contiguous), FP32, in DEVICE memory,
+ *     owned by the caller. The library never frees caller memory.
+ *   - Index sets are 0-based int64 in HOST memory, each strictly increasing. Per set: I_1..I_n
+ *     (|I_i| = nI[i] entries in [0, d_i)) then J_1..J_n (|J_i| = nJ[i] entries in
+ *     [0, prod_{j != i} d_j)). J_i indexes the columns of the mode-i unfolding X_(i) in row-major
+ *     order of the remaining modes (last mode fastest).
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream). Work is stream-ordered; calls
+ *     that return results on the host synchronise `stream` once before returning.
+ *   - No call throws. Every call returns an rtcur_status. Invalid arguments return
+ *     RTCUR_EINVAL before any GPU work; the message is kept per plan (rtcur_last_error).
+ *   - A plan owns all device workspace, sized at rtcur_create; the solve calls allocate
+ *     nothing. A plan is not thread-safe; distinct plans are independent.
+ */
+#ifndef RTCUR_H
+#define RTCUR_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RTCUR_API __attribute__((visibility("default")))
+#else
+#define RTCUR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rtcur_plan rtcur_plan; /* opaque */
+
+typedef enum {
+  RTCUR_OK = 0,
+  RTCUR_NOT_CONVERGED = 1, /* status, not an error: stopped at max_iter with e > tol */
+  RTCUR_EINVAL = -1,       /* invalid argument (message in rtcur_last_error) */
+  RTCUR_ENOMEM = -2,       /* device allocation failed at create */
+  RTCUR_ECUDA = -3,        /* a CUDA runtime call failed */
+  RTCUR_ENONFINITE = -4,   /* NaN or Inf met in X on the sampled entries */
+  RTCUR_ETIMEOUT = -5,     /* a bounded device-side wait gave up */
+  RTCUR_EDEVICE = -6       /* a device-side consistency check failed */
+} rtcur_status;
+
+enum { RTCUR_VARIANT_F = 0, RTCUR_VARIANT_R = 1 };      /* Sec. 3.4: fixed / resampled indices */
+enum { RTCUR_SCOPE_SAMPLED = 0, RTCUR_SCOPE_FULL = 1 }; /* Eq. partial S update / Eq. S=HT(X-L) */
+/* Dense-pass forms (FULL scope): how L^(k) is evaluated when S^(k+1) is formed over the whole
+ * tensor. FP32: the factored last-mode product in FP32 FMA, fused with the threshold (default).
+ * FP32_PLAIN: the literal chain of Eq. (L=CUR) materialised in FP32, then a separate HT pass.
+ * BF16 / TF32: the factored product on tcgen05 tensor cores with FP32 accumulation. */
+enum { RTCUR_FORM_FP32 = 0, RTCUR_FORM_FP32_PLAIN = 1, RTCUR_FORM_BF16 = 2, RTCUR_FORM_TF32 = 3 };
+
+/* Bits of rtcur_result.flags */
+enum {
+  RTCUR_FLAG_RANK_DEFICIENT = 1, /* some SVD_{r_i} kept fewer than r_i singular values */
+  RTCUR_FLAG_TIE = 2             /* some sigma_{r_i} and sigma_{r_i + 1} were not separable */
+};
+
+typedef struct rtcur_options {
+  int32_t scope;             /* RTCUR_SCOPE_*; default SAMPLED */
+  int32_t dense_form;        /* RTCUR_FORM_*; default FP32 (used by the FULL scope only) */
+  int32_t refine_steps;      /* FP64 refinement steps of the truncated pinv; default 2 */
+  int32_t jacobi_max_sweeps; /* cap on FP32 Jacobi sweeps of the pinv; default 30 */
+  double inband_rel;         /* half-width of the reported threshold band, relative to zeta; 1e-6 */
+  int32_t eig_method;        /* FP32 eigenbasis of the pinv: 0 tridiagonal + inverse iteration
+                                (used when every |I_i| <= 128, default), 1 cyclic Jacobi */
+  int32_t reserved[7];       /* must be zero */
+} rtcur_options;
+
+typedef struct rtcur_result {
+  int32_t iters;        /* k at exit */
+  int32_t status;       /* RTCUR_OK or RTCUR_NOT_CONVERGED */
+  int32_t flags;        /* RTCUR_FLAG_* seen in any iteration */
+  int32_t jacobi_sweeps; /* FP32 Jacobi sweeps in the last iteration (max over modes) */
+  double e;             /* e^(k) */
+  double zeta;          /* zeta^(k) */
+  int64_t nnz_sample;   /* nonzeros of S^(k) on the sampled entries (R and fiber segments) */
+  int64_t inband_sample;/* sampled entries with ||X - L^(k-1)| - zeta^(k)| <= inband_rel*zeta^(k) */
+  int64_t nnz_full;     /* FULL scope: nonzeros of S^(k) over the whole tensor; else -1 */
+  int64_t inband_full;  /* FULL scope: the band count over the whole tensor; else -1 */
+  double resid_full;    /* FULL scope: ||X - L^(k-1) - S^(k)||_F^2 over the whole tensor; else -1 */
+  /* Optional per-iteration histories: caller arrays of max_iter entries, or NULL. */
+  double* e_hist;
+  double* zeta_hist;
+  int64_t* nnz_hist;
+} rtcur_result;
+
+/* rtcur_create -- validate the problem geometry and allocate a plan with all its workspace.
+ *   out       receives the plan (set to NULL on failure)
+ *   n_modes   n, 2 <= n <= 4
+ *   dims      n mode sizes d_i >= 1, prod d_i < 2^40
+ *   ranks     n target multilinear ranks r_i, 1 <= r_i <= 16 (Algorithm 1 input)
+ *   nI, nJ    |I_i| in [r_i, min(d_i, 192)], |J_i| in [r_i, min(prod_{j!=i} d_j, 4096)]
+ *             (Sec. 2.2 sample sizes; Sec. 4 uses ceil(v r_i ln d_i) and ceil(v r_i ln prod))
+ *   zeta0     initial threshold; <= 0 means max|X| computed on the device at each solve
+ *   gamma     decay factor, 0 < gamma < 1 (Sec. 3.2)
+ *   tol       target e^(k) (Eq. rel_err); the loop runs while e > tol
+ *   max_iter  1 <= max_iter <= 100000
+ *   variant   RTCUR_VARIANT_F or RTCUR_VARIANT_R (Sec. 3.4)
+ *   opt       NULL for defaults
+ * Errors: RTCUR_EINVAL (bad argument), RTCUR_ENOMEM, RTCUR_ECUDA. */
+RTCUR_API rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims,
+                          const int32_t* ranks, const int32_t* nI, const int32_t* nJ,
+                          double zeta0, double gamma, double tol, int32_t max_iter,
+                          int32_t variant, const rtcur_options* opt);
+
+/* rtcur_solve -- run Algorithm 1 to completion on one tensor.
+ *   X      device, prod d_i floats, caller-owned, read only
+ *   idx    host index sets (layout above): 1 set for variant F, max_iter sets for variant R
+ *          (iteration k uses set k)
+ *   L_out  device, prod d_i floats or NULL: receives L^(k) = R x_i (C_i U_i^+) (Eq. L=CUR)
+ *   S_out  device, prod d_i floats or NULL: receives S^(k) = HT_{zeta^(k)}(X - L^(k-1)) over
+ *          the whole tensor (in the FULL scope it is also the buffer written every iteration)
+ *   res    host, filled on return (may be NULL)
+ * The loop runs on the device as one CUDA graph with a conditional WHILE node; the host
+ * synchronises once at the end. Returns RTCUR_OK or RTCUR_NOT_CONVERGED on success. */
+RTCUR_API rtcur_status rtcur_solve(rtcur_plan* plan, const float* X, const int64_t* idx, float* L_out,
+                         float* S_out, rtcur_result* res, void* stream);
+
+/* Step-wise form of rtcur_solve (same arguments, same semantics):
+ * rtcur_begin uploads the index sets and resets the state to L^(0) = 0, zeta^(0) (no host sync);
+ * rtcur_iterate runs exactly n_iter iterations regardless of tol (no host sync; variant R uses
+ * set (k mod max_iter)); rtcur_finish materialises L_out / S_out, fills res and synchronises. */
+RTCUR_API rtcur_status rtcur_begin(rtcur_plan* plan, const float* X, const int64_t* idx, float* S_work,
+                         void* stream);
+RTCUR_API rtcur_status rtcur_iterate(rtcur_plan* plan, int32_t n_iter, void* stream);
+RTCUR_API rtcur_status rtcur_finish(rtcur_plan* plan, float* L_out, float* S_out, rtcur_result* res,
+                          void* stream);
+
+/* rtcur_threshold_dense -- Step (I) of Algorithm 1 over the whole tensor for the current state:
+ * S_work = HT_{gamma zeta^(k)}(X - L^(k)) (Eq. S=HT(X-L)) with the plan's dense form, n_launch
+ * times (identical launches; for timing the fused pass alone). Needs a FULL-scope plan after
+ * rtcur_begin; writes the S_work buffer given to rtcur_begin and the dense counters that
+ * rtcur_finish reports. Does not advance k. No host sync. */
+RTCUR_API rtcur_status rtcur_threshold_dense(rtcur_plan* plan, int32_t n_launch, void* stream);
+
+/* rtcur_get_factors -- copy the current L^(k) in Tucker form L = G x_1 B_1 ... x_n B_n to host
+ * arrays (FP32): G has prod r_i entries (row-major), B_i is d_i x r_i row-major, packed mode
+ * after mode in B (sum d_i r_i entries). This is the same tensor as R x_i (C_i U_i^+) of
+ * Eq. (L=CUR) (B_i = C_i V_r Sigma_r^-1, G = R x_i Q_{r,i}^T with U_i = Q_r Sigma_r V_r^T).
+ * Also returns k (iterations done) and zeta^(k). Synchronises `stream`. */
+RTCUR_API rtcur_status rtcur_get_factors(rtcur_plan* plan, float* G, float* B, int32_t* k, double* zeta,
+                               void* stream);
+
+/* Sizes of the plan's sampled-entry buffer and of its segments, for callers that read it. */
+RTCUR_API int64_t rtcur_sample_count(const rtcur_plan* plan);
+
+/* Last error message of a plan (NULL plan: the last create failure); never NULL. */
+RTCUR_API const char* rtcur_last_error(const rtcur_plan* plan);
+
+/* Free a plan and its workspace; NULL is allowed. Synchronises the device first. */
+RTCUR_API void rtcur_destroy(rtcur_plan* plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RTCUR_H */

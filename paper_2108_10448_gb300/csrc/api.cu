@@ -1,0 +1,491 @@
+// Host side of librtcur.so: argument validation, plan workspace, CUDA-graph construction and
+// the extern "C" entry points declared in include/rtcur.h.
+//
+// One RTCUR iteration (Algorithm 1's loop body) is one captured graph with two branches that
+// depend only on L^(k):
+//   branch A (FULL scope only): the dense fused threshold pass over the whole tensor;
+//   branch B: sampled threshold -> Gram -> FP32 Jacobi -> FP64 refinement -> B_i -> core G ->
+//             table T -> sampled error e^(k+1).
+// They join before the commit kernel, which advances k and zeta and sets the loop condition.
+// rtcur_solve launches a graph whose single node is a conditional WHILE over that body, so the
+// whole solve runs on the device with one host synchronisation at the end.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/rtcur.h"
+#include "rtcur_internal.cuh"
+
+struct rtcur_plan {
+  Geom g;
+  Bufs b;
+  rtcur_options opt;
+  double zeta0;
+  float* S_internal = nullptr;
+  float* S_work = nullptr;
+  const float* X = nullptr;
+  cudaStream_t cap = nullptr, side = nullptr;
+  cudaEvent_t evFork = nullptr, evJoin = nullptr;
+  cudaGraph_t loopG = nullptr, iterG = nullptr;
+  cudaGraphExec_t loopX = nullptr, iterX = nullptr;
+  std::vector<void*> allocs;
+  std::vector<int> pos_host;
+  std::string err;
+  bool begun = false;
+};
+
+namespace {
+
+thread_local std::string g_create_err = "no error";
+
+rtcur_status fail(rtcur_plan* p, rtcur_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (p) p->err = buf; else g_create_err = buf;
+  return st;
+}
+
+#define CKC(p, call)                                                                     \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(p, RTCUR_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));       \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(rtcur_plan* p, T** ptr, size_t count) {
+  void* v = nullptr;
+  size_t bytes = count * sizeof(T);
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&v, bytes);
+  if (e != cudaSuccess) return e;
+  p->allocs.push_back(v);
+  *ptr = static_cast<T*>(v);
+  return cudaSuccess;
+}
+
+cudaError_t capture_body(rtcur_plan* p, cudaStream_t s, unsigned long long handle, int use_handle) {
+  const Geom& g = p->g;
+  const Bufs& b = p->b;
+  cudaError_t e;
+  const bool full = (g.scope == RTCUR_SCOPE_FULL);
+  if (full) {
+    if ((e = cudaEventRecord(p->evFork, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(p->side, p->evFork, 0)) != cudaSuccess) return e;
+    if ((e = launch_dense(g, b, p->opt.dense_form, p->side)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(p->evJoin, p->side)) != cudaSuccess) return e;
+  }
+  if ((e = launch_sample_ht(g, b, s)) != cudaSuccess) return e;
+  if ((e = launch_gram(g, b, s)) != cudaSuccess) return e;
+  if ((e = launch_jacobi(g, b, s)) != cudaSuccess) return e;
+  if ((e = launch_refine(g, b, s)) != cudaSuccess) return e;
+  if ((e = launch_factor_B(g, b, s)) != cudaSuccess) return e;
+  if ((e = launch_core(g, b, s)) != cudaSuccess) return e;
+  if ((e = launch_table(g, b, 1, s)) != cudaSuccess) return e;
+  if ((e = launch_sample_err(g, b, s)) != cudaSuccess) return e;
+  if (full && (e = cudaStreamWaitEvent(s, p->evJoin, 0)) != cudaSuccess) return e;
+  return launch_commit(g, b, handle, use_handle, s);
+}
+
+rtcur_status build_graphs(rtcur_plan* p) {
+  if (p->iterX) return RTCUR_OK;
+  // single-iteration graph (rtcur_iterate)
+  CKC(p, cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = capture_body(p, p->cap, 0ull, 0);
+  cudaGraph_t gr = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(p->cap, &gr);
+  if (e != cudaSuccess) return fail(p, RTCUR_ECUDA, "capturing the iteration: %s", cudaGetErrorString(e));
+  if (e2 != cudaSuccess) return fail(p, RTCUR_ECUDA, "ending capture: %s", cudaGetErrorString(e2));
+  p->iterG = gr;
+  CKC(p, cudaGraphInstantiate(&p->iterX, p->iterG, 0));
+  // WHILE-loop graph (rtcur_solve): body = the same iteration, condition set by the commit kernel
+  CKC(p, cudaGraphCreate(&p->loopG, 0));
+  cudaGraphConditionalHandle h;
+  CKC(p, cudaGraphConditionalHandleCreate(&h, p->loopG, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  CKC(p, cudaGraphAddNode(&node, p->loopG, nullptr, nullptr, 0, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  CKC(p, cudaStreamBeginCaptureToGraph(p->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  e = capture_body(p, p->cap, (unsigned long long)h, 1);
+  e2 = cudaStreamEndCapture(p->cap, &gr);
+  if (e != cudaSuccess) return fail(p, RTCUR_ECUDA, "capturing the loop body: %s", cudaGetErrorString(e));
+  if (e2 != cudaSuccess) return fail(p, RTCUR_ECUDA, "ending body capture: %s", cudaGetErrorString(e2));
+  CKC(p, cudaGraphInstantiate(&p->loopX, p->loopG, 0));
+  return RTCUR_OK;
+}
+
+rtcur_status check_sets(rtcur_plan* p, const int64_t* idx) {
+  const Geom& g = p->g;
+  for (int s = 0; s < g.n_sets; ++s) {
+    const int64_t* set = idx + (size_t)s * g.set_len;
+    for (int i = 0; i < g.n; ++i) {
+      long long other = g.N / g.d[i];
+      const int64_t* I = set + g.ioff[i];
+      const int64_t* J = set + g.joff[i];
+      for (int a = 0; a < g.m[i]; ++a) {
+        if (I[a] < 0 || I[a] >= g.d[i] || (a > 0 && I[a] <= I[a - 1]))
+          return fail(p, RTCUR_EINVAL, "set %d: I_%d must be strictly increasing in [0, %lld)", s, i + 1, g.d[i]);
+      }
+      for (int a = 0; a < g.q[i]; ++a) {
+        if (J[a] < 0 || J[a] >= other || (a > 0 && J[a] <= J[a - 1]))
+          return fail(p, RTCUR_EINVAL, "set %d: J_%d must be strictly increasing in [0, %lld)", s, i + 1, other);
+      }
+    }
+  }
+  return RTCUR_OK;
+}
+
+bool aligned16(const void* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15u) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims,
+                          const int32_t* ranks, const int32_t* nI, const int32_t* nJ,
+                          double zeta0, double gamma, double tol, int32_t max_iter,
+                          int32_t variant, const rtcur_options* opt) {
+  if (!out) return fail(nullptr, RTCUR_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n_modes < 2 || n_modes > RT_MAXN) return fail(nullptr, RTCUR_EINVAL, "n_modes must be in [2, %d]", RT_MAXN);
+  if (!dims || !ranks || !nI || !nJ) return fail(nullptr, RTCUR_EINVAL, "dims, ranks, nI and nJ must not be NULL");
+  if (!(gamma > 0.0 && gamma < 1.0)) return fail(nullptr, RTCUR_EINVAL, "gamma must be in (0, 1)");
+  if (!(tol >= 0.0) || std::isinf(tol)) return fail(nullptr, RTCUR_EINVAL, "tol must be finite and >= 0");
+  if (std::isnan(zeta0) || std::isinf(zeta0)) return fail(nullptr, RTCUR_EINVAL, "zeta0 must be finite");
+  if (max_iter < 1 || max_iter > 100000) return fail(nullptr, RTCUR_EINVAL, "max_iter must be in [1, 100000]");
+  if (variant != RTCUR_VARIANT_F && variant != RTCUR_VARIANT_R) return fail(nullptr, RTCUR_EINVAL, "variant must be F (0) or R (1)");
+  rtcur_options o;
+  memset(&o, 0, sizeof o);
+  o.scope = RTCUR_SCOPE_SAMPLED;
+  o.dense_form = RTCUR_FORM_FP32;
+  o.refine_steps = 2;
+  o.jacobi_max_sweeps = 30;
+  o.inband_rel = 1e-6;
+  if (opt) {
+    o = *opt;
+    for (int i = 0; i < 7; ++i)
+      if (o.reserved[i] != 0) return fail(nullptr, RTCUR_EINVAL, "options.reserved must be zero");
+    if (o.refine_steps == 0 && o.jacobi_max_sweeps == 0 && o.inband_rel == 0.0) {
+      o.refine_steps = 2; o.jacobi_max_sweeps = 30; o.inband_rel = 1e-6;
+    }
+  }
+  if (o.scope != RTCUR_SCOPE_SAMPLED && o.scope != RTCUR_SCOPE_FULL) return fail(nullptr, RTCUR_EINVAL, "scope must be SAMPLED or FULL");
+  if (o.dense_form != RTCUR_FORM_FP32) return fail(nullptr, RTCUR_EINVAL, "dense_form %d is not available in this build", o.dense_form);
+  if (o.refine_steps < 0 || o.refine_steps > 8) return fail(nullptr, RTCUR_EINVAL, "refine_steps must be in [0, 8]");
+  if (o.jacobi_max_sweeps < 1 || o.jacobi_max_sweeps > 100) return fail(nullptr, RTCUR_EINVAL, "jacobi_max_sweeps must be in [1, 100]");
+  if (!(o.inband_rel >= 0.0 && o.inband_rel < 1.0)) return fail(nullptr, RTCUR_EINVAL, "inband_rel must be in [0, 1)");
+  if (o.eig_method != 0 && o.eig_method != 1) return fail(nullptr, RTCUR_EINVAL, "eig_method must be 0 (tridiagonal) or 1 (Jacobi)");
+
+  Geom g;
+  memset(&g, 0, sizeof g);
+  g.n = n_modes;
+  g.N = 1;
+  for (int i = 0; i < n_modes; ++i) {
+    if (dims[i] < 1) return fail(nullptr, RTCUR_EINVAL, "dims[%d] must be >= 1", i);
+    g.d[i] = dims[i];
+    if (g.N > (1LL << 40) / dims[i]) return fail(nullptr, RTCUR_EINVAL, "prod(dims) must be < 2^40");
+    g.N *= dims[i];
+  }
+  for (int i = 0; i < n_modes; ++i) {
+    long long other = g.N / g.d[i];
+    if (ranks[i] < 1 || ranks[i] > RT_MAXR) return fail(nullptr, RTCUR_EINVAL, "ranks[%d] must be in [1, %d]", i, RT_MAXR);
+    if (nI[i] < ranks[i] || nI[i] > g.d[i] || nI[i] > RT_MAXM)
+      return fail(nullptr, RTCUR_EINVAL, "nI[%d] must be in [ranks[%d], min(dims[%d], %d)]", i, i, i, RT_MAXM);
+    if (nJ[i] < ranks[i] || nJ[i] > other || nJ[i] > RT_MAXQ)
+      return fail(nullptr, RTCUR_EINVAL, "nJ[%d] must be in [ranks[%d], min(prod of other dims, %d)]", i, i, RT_MAXQ);
+    g.r[i] = ranks[i];
+    g.m[i] = nI[i];
+    g.q[i] = nJ[i];
+  }
+  g.variant = variant;
+  g.n_sets = (variant == RTCUR_VARIANT_R) ? max_iter : 1;
+  g.max_iter = max_iter;
+  g.scope = o.scope;
+  g.refine_steps = o.refine_steps;
+  g.max_sweeps = o.jacobi_max_sweeps;
+  g.warm_start = 0;
+  g.eig_method = o.eig_method;
+  g.gamma = gamma;
+  g.tol = tol;
+  g.inband = o.inband_rel;
+  g.nR = 1;
+  g.nG = 1;
+  for (int i = 0; i < n_modes; ++i) {
+    g.nR *= g.m[i];
+    g.nG *= g.r[i];
+  }
+  g.rlast = g.r[n_modes - 1];
+  g.seg[0] = 0;
+  g.seg[1] = g.nR;
+  for (int i = 0; i < n_modes; ++i) g.seg[i + 2] = g.seg[i + 1] + g.d[i] * g.q[i];
+  g.nS = g.seg[n_modes + 1];
+  g.rowsT = g.N / g.d[n_modes - 1];
+  long long off = 0;
+  for (int i = 0; i < n_modes; ++i) { g.ioff[i] = off; off += g.m[i]; }
+  for (int i = 0; i < n_modes; ++i) { g.joff[i] = off; off += g.q[i]; }
+  g.set_len = off;
+  long long oB = 0, oQ = 0, oM = 0, oY = 0, oR = 0, oL = 0, nch = 1;
+  for (int i = 0; i < n_modes; ++i) {
+    g.offB[i] = oB; oB += g.d[i] * g.r[i];
+    g.offQ[i] = oQ; oQ += (long long)g.m[i] * g.r[i];
+    g.offM[i] = oM; oM += (long long)g.m[i] * g.m[i];
+    g.offY[i] = oY; oY += (long long)g.q[i] * g.r[i];
+    g.offR[i] = oR; oR += g.r[i];
+    g.offL[i] = oL; oL += g.m[i];
+    long long c = (g.q[i] + 31) / 32;
+    if (c > nch) nch = c;
+  }
+  g.sumB = oB;
+  g.sumMR = oQ;
+  {
+    long long oD = 0, oW = 0;
+    for (int i = 0; i < n_modes; ++i) {
+      g.offD[i] = oD; oD += g.d[i];
+      g.offW[i] = oW; oW += (long long)g.m[i] * g.q[i];
+      if (g.d[i] * (long long)g.q[i] >= (1LL << 31))
+        return fail(nullptr, RTCUR_EINVAL, "dims[%d] * nJ[%d] must be < 2^31", i, i);
+    }
+    g.sumD = oD;
+    g.sumW = oW;
+  }
+  g.nchunk = nch;
+  g.nH = (long long)g.r[0] * g.r[n_modes - 1];
+  for (int l = 1; l <= n_modes - 2; ++l) g.nH *= g.d[l];
+  long long zs = 1;
+  for (int st = 0; st < n_modes - 1; ++st) {
+    int j = n_modes - 1 - st;
+    long long sz = 1;
+    for (int l = 0; l < n_modes; ++l) sz *= (l >= j) ? g.r[l] : g.m[l];
+    if (sz > zs) zs = sz;
+  }
+  g.zsize = zs;
+
+  if (g.rowsT >= (1LL << 32) || g.d[n_modes - 1] >= (1LL << 32))
+    return fail(nullptr, RTCUR_EINVAL, "prod of the first n-1 dims and the last dim must be < 2^32");
+  int dev = 0, optin = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce != cudaSuccess) return fail(nullptr, RTCUR_ECUDA, "no CUDA device: %s", cudaGetErrorString(ce));
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  int mx = 0;
+  for (int i = 0; i < n_modes; ++i) mx = g.m[i] > mx ? g.m[i] : mx;
+  if (jacobi_smem_bytes(mx) > (size_t)optin)
+    return fail(nullptr, RTCUR_EINVAL, "|I_i| = %d needs %zu bytes of shared memory (device allows %d)", mx, jacobi_smem_bytes(mx), optin);
+
+  rtcur_plan* p = new rtcur_plan();
+  p->g = g;
+  p->opt = o;
+  p->zeta0 = zeta0;
+  Bufs& b = p->b;
+  memset(&b, 0, sizeof b);
+  cudaError_t e = cudaSuccess;
+#define AL(ptr, cnt) if (e == cudaSuccess) e = dalloc(p, &(ptr), (size_t)(cnt))
+  AL(b.st, 1);
+  AL(b.sp, 1);
+  long long* idx = nullptr;
+  AL(idx, (size_t)g.n_sets * g.set_len);
+  b.idx = idx;
+  AL(b.Xs, g.nS);
+  AL(b.XS, g.nS);
+  AL(b.rc, g.nS);
+  AL(b.W, g.sumW);
+  int* posd = nullptr;
+  AL(posd, (size_t)g.n_sets * g.sumD);
+  b.pos = posd;
+  AL(b.gram, oM);
+  AL(b.jV, oM);
+  AL(b.jL, oL);
+  AL(b.X1, oQ);
+  AL(b.Qr, oQ);
+  AL(b.sig, oR);
+  AL(b.Y, oY);
+  AL(b.ework, 3 * oQ);
+  AL(b.Bpart, g.nchunk * g.sumB);
+  AL(b.B[0], g.sumB);
+  AL(b.B[1], g.sumB);
+  AL(b.G[0], g.nG);
+  AL(b.G[1], g.nG);
+  AL(b.Z[0], g.zsize);
+  AL(b.Z[1], g.zsize);
+  AL(b.H, g.nH);
+  AL(b.T[0], g.rowsT * g.rlast + 4);  // +4: the dense pass copies 16-byte aligned windows
+  AL(b.T[1], g.rowsT * g.rlast + 4);
+  AL(b.red, (size_t)TK_COUNT * 1024 * RT_RED_SLOTS);
+  AL(b.ticket, TK_COUNT);
+  AL(b.e_hist, max_iter);
+  AL(b.z_hist, max_iter);
+  AL(b.nnz_hist, max_iter);
+  if (o.scope == RTCUR_SCOPE_FULL) AL(p->S_internal, g.N);
+#undef AL
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->evFork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->evJoin, cudaEventDisableTiming);
+  if (e == cudaSuccess) {
+    size_t sm = jacobi_smem_bytes(mx);
+    e = prepare_jacobi(sm);
+  }
+  if (e == cudaSuccess) e = prepare_dense(g);
+  if (e == cudaSuccess) e = prepare_refine(g);
+  if (e == cudaSuccess) e = cudaMemset(b.ticket, 0, sizeof(unsigned) * TK_COUNT);
+  if (e != cudaSuccess) {
+    rtcur_status st = (e == cudaErrorMemoryAllocation) ? RTCUR_ENOMEM : RTCUR_ECUDA;
+    fail(nullptr, st, "allocating the plan: %s", cudaGetErrorString(e));
+    rtcur_destroy(p);
+    return st;
+  }
+  *out = p;
+  return RTCUR_OK;
+}
+
+rtcur_status rtcur_begin(rtcur_plan* p, const float* X, const int64_t* idx, float* S_work,
+                         void* stream) {
+  if (!p) return fail(nullptr, RTCUR_EINVAL, "plan is NULL");
+  if (!X || !idx) return fail(p, RTCUR_EINVAL, "X and idx must not be NULL");
+  const Geom& g = p->g;
+  float* S = S_work ? S_work : p->S_internal;
+  if (!aligned16(X) || (S && !aligned16(S))) return fail(p, RTCUR_EINVAL, "X and S must be 16-byte aligned");
+  rtcur_status st = check_sets(p, idx);
+  if (st != RTCUR_OK) return st;
+  rtcur_status gb = build_graphs(p);
+  if (gb != RTCUR_OK) return gb;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Bufs& b = p->b;
+  CKC(p, cudaMemcpyAsync((void*)b.idx, idx, sizeof(int64_t) * g.n_sets * g.set_len, cudaMemcpyHostToDevice, s));
+  // position tables: pos[t] = a if I_i[a] = t, else -1 (one table per set)
+  p->pos_host.assign((size_t)g.n_sets * g.sumD, -1);
+  for (int st2 = 0; st2 < g.n_sets; ++st2) {
+    const int64_t* set = idx + (size_t)st2 * g.set_len;
+    for (int i = 0; i < g.n; ++i)
+      for (int a = 0; a < g.m[i]; ++a)
+        p->pos_host[(size_t)st2 * g.sumD + g.offD[i] + set[g.ioff[i] + a]] = a;
+  }
+  CKC(p, cudaMemcpyAsync((void*)b.pos, p->pos_host.data(), sizeof(int) * p->pos_host.size(), cudaMemcpyHostToDevice, s));
+  SolvePtrs sp;
+  sp.X = X;
+  sp.S = S;
+  CKC(p, cudaMemcpyAsync(b.sp, &sp, sizeof sp, cudaMemcpyHostToDevice, s));
+  CKC(p, cudaMemsetAsync(b.T[0], 0, sizeof(float) * g.rowsT * g.rlast, s));
+  CKC(p, cudaMemsetAsync(b.B[0], 0, sizeof(float) * g.sumB, s));
+  CKC(p, cudaMemsetAsync(b.G[0], 0, sizeof(float) * g.nG, s));
+  CKC(p, launch_setup(g, b, p->zeta0, p->zeta0 <= 0.0 ? 1 : 0, s));
+  if (g.variant == RTCUR_VARIANT_F) CKC(p, launch_gather_x(g, b, s));
+  p->X = X;
+  p->S_work = S;
+  p->begun = true;
+  return RTCUR_OK;
+}
+
+rtcur_status rtcur_iterate(rtcur_plan* p, int32_t n_iter, void* stream) {
+  if (!p) return fail(nullptr, RTCUR_EINVAL, "plan is NULL");
+  if (!p->begun) return fail(p, RTCUR_EINVAL, "rtcur_begin must come first");
+  if (n_iter < 0) return fail(p, RTCUR_EINVAL, "n_iter must be >= 0");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int i = 0; i < n_iter; ++i) CKC(p, cudaGraphLaunch(p->iterX, s));
+  return RTCUR_OK;
+}
+
+rtcur_status rtcur_finish(rtcur_plan* p, float* L_out, float* S_out, rtcur_result* res,
+                          void* stream) {
+  if (!p) return fail(nullptr, RTCUR_EINVAL, "plan is NULL");
+  if (!p->begun) return fail(p, RTCUR_EINVAL, "rtcur_begin must come first");
+  if ((L_out && !aligned16(L_out)) || (S_out && !aligned16(S_out)))
+    return fail(p, RTCUR_EINVAL, "L_out and S_out must be 16-byte aligned");
+  const Geom& g = p->g;
+  const Bufs& b = p->b;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool full = (g.scope == RTCUR_SCOPE_FULL);
+  CKC(p, launch_materialize(g, b, L_out, full ? nullptr : S_out, s));
+  if (full && S_out && S_out != p->S_work)
+    CKC(p, cudaMemcpyAsync(S_out, p->S_work, sizeof(float) * g.N, cudaMemcpyDeviceToDevice, s));
+  State h;
+  CKC(p, cudaMemcpyAsync(&h, b.st, sizeof h, cudaMemcpyDeviceToHost, s));
+  CKC(p, cudaStreamSynchronize(s));
+  int nh = h.k < g.max_iter ? h.k : g.max_iter;
+  if (res) {
+    if (res->e_hist && nh) CKC(p, cudaMemcpy(res->e_hist, b.e_hist, sizeof(double) * nh, cudaMemcpyDeviceToHost));
+    if (res->zeta_hist && nh) CKC(p, cudaMemcpy(res->zeta_hist, b.z_hist, sizeof(double) * nh, cudaMemcpyDeviceToHost));
+    if (res->nnz_hist && nh) CKC(p, cudaMemcpy(res->nnz_hist, b.nnz_hist, sizeof(int64_t) * nh, cudaMemcpyDeviceToHost));
+    res->iters = h.k;
+    res->flags = h.flags;
+    res->jacobi_sweeps = h.jsweeps;
+    res->e = h.e;
+    res->zeta = h.zeta;
+    res->nnz_sample = h.nnz_s;
+    res->inband_sample = h.inband_s;
+    res->nnz_full = full ? h.nnz_f : -1;
+    res->inband_full = full ? h.inband_f : -1;
+    res->resid_full = full ? h.resid_f : -1.0;
+    res->status = (h.e > g.tol) ? RTCUR_NOT_CONVERGED : RTCUR_OK;
+  }
+  if (h.err != 0) {
+    if (h.err == RTCUR_ENONFINITE) return fail(p, RTCUR_ENONFINITE, "X holds NaN or Inf on the sampled entries");
+    return fail(p, (rtcur_status)h.err, "device-side error %d", h.err);
+  }
+  return (h.e > g.tol) ? RTCUR_NOT_CONVERGED : RTCUR_OK;
+}
+
+rtcur_status rtcur_solve(rtcur_plan* p, const float* X, const int64_t* idx, float* L_out,
+                         float* S_out, rtcur_result* res, void* stream) {
+  rtcur_status st = rtcur_begin(p, X, idx, (p && p->g.scope == RTCUR_SCOPE_FULL) ? S_out : nullptr, stream);
+  if (st != RTCUR_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (1.0 > p->g.tol) CKC(p, cudaGraphLaunch(p->loopX, s));
+  return rtcur_finish(p, L_out, S_out, res, stream);
+}
+
+rtcur_status rtcur_threshold_dense(rtcur_plan* p, int32_t n_launch, void* stream) {
+  if (!p) return fail(nullptr, RTCUR_EINVAL, "plan is NULL");
+  if (!p->begun) return fail(p, RTCUR_EINVAL, "rtcur_begin must come first");
+  if (p->g.scope != RTCUR_SCOPE_FULL) return fail(p, RTCUR_EINVAL, "rtcur_threshold_dense needs a FULL-scope plan");
+  if (n_launch < 0) return fail(p, RTCUR_EINVAL, "n_launch must be >= 0");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int i = 0; i < n_launch; ++i) CKC(p, launch_dense(p->g, p->b, p->opt.dense_form, s));
+  return RTCUR_OK;
+}
+
+rtcur_status rtcur_get_factors(rtcur_plan* p, float* G, float* B, int32_t* k, double* zeta,
+                               void* stream) {
+  if (!p) return fail(nullptr, RTCUR_EINVAL, "plan is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  State h;
+  CKC(p, cudaMemcpyAsync(&h, p->b.st, sizeof h, cudaMemcpyDeviceToHost, s));
+  CKC(p, cudaStreamSynchronize(s));
+  int cp = h.k & 1;
+  if (G) CKC(p, cudaMemcpy(G, p->b.G[cp], sizeof(float) * p->g.nG, cudaMemcpyDeviceToHost));
+  if (B) CKC(p, cudaMemcpy(B, p->b.B[cp], sizeof(float) * p->g.sumB, cudaMemcpyDeviceToHost));
+  if (k) *k = h.k;
+  if (zeta) *zeta = h.zeta;
+  return RTCUR_OK;
+}
+
+int64_t rtcur_sample_count(const rtcur_plan* p) { return p ? p->g.nS : 0; }
+
+const char* rtcur_last_error(const rtcur_plan* p) { return p ? p->err.c_str() : g_create_err.c_str(); }
+
+void rtcur_destroy(rtcur_plan* p) {
+  if (!p) return;
+  cudaDeviceSynchronize();
+  if (p->loopX) cudaGraphExecDestroy(p->loopX);
+  if (p->iterX) cudaGraphExecDestroy(p->iterX);
+  if (p->loopG) cudaGraphDestroy(p->loopG);
+  if (p->iterG) cudaGraphDestroy(p->iterG);
+  if (p->evFork) cudaEventDestroy(p->evFork);
+  if (p->evJoin) cudaEventDestroy(p->evJoin);
+  if (p->cap) cudaStreamDestroy(p->cap);
+  if (p->side) cudaStreamDestroy(p->side);
+  for (void* v : p->allocs) cudaFree(v);
+  delete p;
+}
+
+}  // extern "C"

@@ -1,0 +1,489 @@
+// Dense fused pass (FULL scope): Step (I) of Algorithm 1 over the whole tensor,
+//   S^(k+1) = HT_{zeta^(k+1)}(X - L^(k))          (Eq. S=HT(X-L), HT of Sec. 3.2)
+// with L^(k) evaluated on the fly as the last-mode product of the table T and B_n, and the
+// reductions ||X - L - S||_F^2, nnz(S) and the threshold-band count fused in. X is read once
+// and S written once: 8 bytes of HBM traffic per element, so the kernel is bandwidth-bound.
+//
+// Mapping: the tensor is viewed as rowsT rows of d_n contiguous floats. A block owns a chunk of
+// float4 columns and strides over rows; each thread keeps its four columns of B_n in registers
+// for the whole launch, so the inner loop reads only X, one broadcast row of T, and writes S.
+// Blocks use few threads per SM so that the latency-bound sampled chain, which runs
+// concurrently on its own graph branch, finds room.
+#include "rtcur_internal.cuh"
+
+namespace {
+
+constexpr int kMaxRedBlocks = 1024;
+constexpr int kRowUnroll = 4;
+
+__device__ __forceinline__ double block_sum_d(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)((blockDim.x + 31) >> 5); ++i) t += sh[i];
+  return t;
+}
+
+__device__ __forceinline__ void ht_acc(float x, float L, float zf, float band, float& s,
+                                       float& res, unsigned& nnz, unsigned& inb) {
+  float dl = x - L;
+  float ad = fabsf(dl);
+  bool keep = ad > zf;
+  s = keep ? dl : 0.f;
+  res = keep ? res : fmaf(dl, dl, res);
+  nnz += keep ? 1u : 0u;
+  inb += (fabsf(ad - zf) <= band) ? 1u : 0u;
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(512) k_dense_fp32(Geom g, Bufs b) {
+  __shared__ double sh[32];
+  const State* st = b.st;
+  const int cur = st->k & 1;
+  const double zeta = g.gamma * st->zeta;
+  const float zf = (float)zeta;
+  const float band = (float)(g.inband * zeta);
+  const float* __restrict__ X = b.sp->X;
+  float* __restrict__ S = b.sp->S;
+  const float* __restrict__ T = b.T[cur];
+  const float* __restrict__ Bn = b.B[cur] + g.offB[g.n - 1];
+  const int rn = g.rlast;
+  const long long dn = g.d[g.n - 1];
+  const long long rows = g.rowsT;
+  float res = 0.f;
+  unsigned nnz = 0u, inb = 0u;
+  if (VEC) {
+    const long long n4 = dn >> 2;
+    const long long c4 = (long long)blockIdx.y * blockDim.x + threadIdx.x;
+    if (c4 < n4) {
+      float br[4][RT_MAXR];
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int c = 0; c < RT_MAXR; ++c) br[j][c] = (c < rn) ? __ldg(Bn + (c4 * 4 + j) * rn + c) : 0.f;
+      const float4* X4 = reinterpret_cast<const float4*>(X);
+      float4* S4 = reinterpret_cast<float4*>(S);
+      for (long long r0 = blockIdx.x; r0 < rows; r0 += (long long)gridDim.x * kRowUnroll) {
+        float4 xv[kRowUnroll];
+#pragma unroll
+        for (int u = 0; u < kRowUnroll; ++u) {
+          long long r = r0 + (long long)u * gridDim.x;
+          if (r < rows) xv[u] = __ldcs(X4 + r * n4 + c4);
+        }
+#pragma unroll
+        for (int u = 0; u < kRowUnroll; ++u) {
+          long long r = r0 + (long long)u * gridDim.x;
+          if (r < rows) {
+            const float* tr = T + r * rn;
+            float L0 = 0.f, L1 = 0.f, L2 = 0.f, L3 = 0.f;
+#pragma unroll
+            for (int c = 0; c < RT_MAXR; ++c) {
+              if (c < rn) {
+                float t = __ldg(tr + c);
+                L0 = fmaf(t, br[0][c], L0);
+                L1 = fmaf(t, br[1][c], L1);
+                L2 = fmaf(t, br[2][c], L2);
+                L3 = fmaf(t, br[3][c], L3);
+              }
+            }
+            float4 sv;
+            ht_acc(xv[u].x, L0, zf, band, sv.x, res, nnz, inb);
+            ht_acc(xv[u].y, L1, zf, band, sv.y, res, nnz, inb);
+            ht_acc(xv[u].z, L2, zf, band, sv.z, res, nnz, inb);
+            ht_acc(xv[u].w, L3, zf, band, sv.w, res, nnz, inb);
+            __stcs(S4 + r * n4 + c4, sv);
+          }
+        }
+      }
+    }
+  } else {
+    const long long col = (long long)blockIdx.y * blockDim.x + threadIdx.x;
+    if (col < dn) {
+      float br[RT_MAXR];
+#pragma unroll
+      for (int c = 0; c < RT_MAXR; ++c) br[c] = (c < rn) ? __ldg(Bn + col * rn + c) : 0.f;
+      for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+        float x = __ldcs(X + r * dn + col);
+        const float* tr = T + r * rn;
+        float L = 0.f;
+#pragma unroll
+        for (int c = 0; c < RT_MAXR; ++c)
+          if (c < rn) L = fmaf(__ldg(tr + c), br[c], L);
+        float s;
+        ht_acc(x, L, zf, band, s, res, nnz, inb);
+        __stcs(S + r * dn + col, s);
+      }
+    }
+  }
+  double* part = b.red + (size_t)TK_DENSE * kMaxRedBlocks * RT_RED_SLOTS;
+  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+  double t0 = block_sum_d((double)res, sh);
+  if (threadIdx.x == 0) part[bid * RT_RED_SLOTS + 0] = t0;
+  t0 = block_sum_d((double)nnz, sh);
+  if (threadIdx.x == 0) part[bid * RT_RED_SLOTS + 1] = t0;
+  t0 = block_sum_d((double)inb, sh);
+  if (threadIdx.x == 0) part[bid * RT_RED_SLOTS + 2] = t0;
+  if (last_block_arrive(b.ticket + TK_DENSE)) {
+    State* w = b.st;
+    const int nb = gridDim.x * gridDim.y;
+    for (int slot = 0; slot < 3; ++slot) {
+      double acc = 0.0;
+      for (int i2 = threadIdx.x; i2 < nb; i2 += blockDim.x) acc += part[i2 * RT_RED_SLOTS + slot];
+      acc = block_sum_d(acc, sh);
+      if (threadIdx.x == 0) {
+        if (slot == 0) w->resid_f = acc;
+        if (slot == 1) w->nnz_f = (long long)acc;
+        if (slot == 2) w->inband_f = (long long)acc;
+      }
+    }
+    if (threadIdx.x == 0) b.ticket[TK_DENSE] = 0u;
+  }
+}
+
+// ---------------------------------------------------------------- TMA-fed fused pass
+// Persistent CTAs (144 of the 152 SMs, one CTA per SM by shared-memory footprint, so a few SMs
+// stay free for the concurrent sampled chain). Each CTA streams tiles of `tr` whole rows of X
+// (tr * d_n floats, ~32 KB) into a kStages-deep shared-memory ring with 1-D cp.async.bulk
+// copies completed on mbarriers; one thread per float4 column computes L from its register
+// copy of B_n and the tile's rows of T, thresholds, and stores S with streaming stores.
+// Every mbarrier wait is bounded: on expiry the kernel records RTCUR_ETIMEOUT, drains its own
+// copies (again bounded) and returns.
+constexpr int kStages = 4;
+constexpr long long kSpinLimit = 1LL << 26;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
+  for (long long i = 0; i < kSpinLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+template <int RN>
+__global__ void __launch_bounds__(1024, 1) k_dense_tma(Geom g, Bufs b, int tr) {
+  extern __shared__ __align__(128) unsigned char dsm[];
+  __shared__ unsigned long long full[kStages];
+  __shared__ double sh[32];
+  __shared__ int abort_flag;
+  const State* st = b.st;
+  const int cur = st->k & 1;
+  const double zeta = g.gamma * st->zeta;
+  const float zf = (float)zeta;
+  const float band = (float)(g.inband * zeta);
+  const float* __restrict__ X = b.sp->X;
+  float* __restrict__ S = b.sp->S;
+  const float* __restrict__ T = b.T[cur];
+  const float* __restrict__ Bn = b.B[cur] + g.offB[g.n - 1];
+  const long long dn = g.d[g.n - 1];
+  const int n4 = (int)(dn >> 2);
+  const long long rows = g.rowsT;
+  const long long ntiles = (rows + tr - 1) / tr;
+  const unsigned tile_bytes_full = (unsigned)(tr * dn * 4);
+  float4* ring = reinterpret_cast<float4*>(dsm);
+  const int stage_f4 = tr * n4;
+  // T rows of a tile: floats [r0*RN rounded down to 4, (r0+nr)*RN rounded up to 4)
+  const int tstage = ((tr * RN + 3) & ~3) + 4;
+  float* tring = reinterpret_cast<float*>(ring + (size_t)kStages * stage_f4);
+  const int c4 = threadIdx.x;
+  float br[4][RN];
+  if (c4 < n4) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int c = 0; c < RN; ++c) br[j][c] = __ldg(Bn + ((long long)c4 * 4 + j) * RN + c);
+  }
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int i = 0; i < kStages; ++i) mbar_init(&full[i], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  // prologue: first kStages tiles of this CTA. Thread 0 alone issues copies and counts, per
+  // stage, the copies issued and the completions it has observed (for the bounded drain).
+  long long my_first = blockIdx.x;
+  int issued[kStages], seen[kStages];
+#pragma unroll
+  for (int s = 0; s < kStages; ++s) issued[s] = seen[s] = 0;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int s = 0; s < kStages; ++s) {
+      long long t = my_first + (long long)s * gridDim.x;
+      if (t < ntiles) {
+        long long r0 = t * tr;
+        long long nr = (r0 + tr <= rows ? tr : rows - r0);
+        unsigned bytes = (unsigned)(nr * dn * 4);
+        long long a0 = (r0 * RN) & ~3LL, a1 = ((r0 + nr) * RN + 3) & ~3LL;
+        unsigned tbytes = (unsigned)((a1 - a0) * 4);
+        mbar_expect_tx(&full[s], bytes + tbytes);
+        bulk_g2s(ring + (size_t)s * stage_f4, X + r0 * dn, bytes, &full[s]);
+        bulk_g2s(tring + (size_t)s * tstage, T + a0, tbytes, &full[s]);
+        issued[s] = 1;
+      }
+    }
+  }
+  float res = 0.f;
+  unsigned nnz = 0u, inb = 0u;
+  int it = 0;
+  for (long long t = my_first; t < ntiles; t += gridDim.x, ++it) {
+    const int s = it % kStages;
+    const unsigned par = (unsigned)((it / kStages) & 1);
+    if (!mbar_wait_bounded(&full[s], par)) {
+      abort_flag = 1;
+    } else if (threadIdx.x == 0) {
+#pragma unroll
+      for (int s2 = 0; s2 < kStages; ++s2) seen[s2] += (s2 == s) ? 1 : 0;
+    }
+    __syncthreads();
+    if (abort_flag) break;
+    const long long r0 = t * tr;
+    const int nr = (int)(r0 + tr <= rows ? tr : rows - r0);
+    if (c4 < n4) {
+      const float4* tile = ring + (size_t)s * stage_f4;
+      const float* ttile = tring + (size_t)s * tstage + (r0 * RN - ((r0 * RN) & ~3LL));
+      for (int rr = 0; rr < nr; ++rr) {
+        const long long r = r0 + rr;
+        float tv[RN];
+#pragma unroll
+        for (int c = 0; c < RN; ++c) tv[c] = ttile[rr * RN + c];
+        float L0 = 0.f, L1 = 0.f, L2 = 0.f, L3 = 0.f;
+#pragma unroll
+        for (int c = 0; c < RN; ++c) {
+          L0 = fmaf(tv[c], br[0][c], L0);
+          L1 = fmaf(tv[c], br[1][c], L1);
+          L2 = fmaf(tv[c], br[2][c], L2);
+          L3 = fmaf(tv[c], br[3][c], L3);
+        }
+        float4 xv = tile[rr * n4 + c4];
+        float4 sv;
+        ht_acc(xv.x, L0, zf, band, sv.x, res, nnz, inb);
+        ht_acc(xv.y, L1, zf, band, sv.y, res, nnz, inb);
+        ht_acc(xv.z, L2, zf, band, sv.z, res, nnz, inb);
+        ht_acc(xv.w, L3, zf, band, sv.w, res, nnz, inb);
+        __stcs(reinterpret_cast<float4*>(S + r * dn) + c4, sv);
+      }
+    }
+    __syncthreads();  // stage s fully consumed
+    if (threadIdx.x == 0) {
+      long long tn = t + (long long)kStages * gridDim.x;
+      if (tn < ntiles) {
+        long long rn0 = tn * tr;
+        long long nr2 = (rn0 + tr <= rows ? tr : rows - rn0);
+        unsigned bytes = (unsigned)(nr2 * dn * 4);
+        long long a0 = (rn0 * RN) & ~3LL, a1 = ((rn0 + nr2) * RN + 3) & ~3LL;
+        unsigned tbytes = (unsigned)((a1 - a0) * 4);
+        mbar_expect_tx(&full[s], bytes + tbytes);
+        bulk_g2s(ring + (size_t)s * stage_f4, X + rn0 * dn, bytes, &full[s]);
+        bulk_g2s(tring + (size_t)s * tstage, T + a0, tbytes, &full[s]);
+#pragma unroll
+        for (int s2 = 0; s2 < kStages; ++s2) issued[s2] += (s2 == s) ? 1 : 0;
+      }
+    }
+  }
+  if (abort_flag) {
+    // drain: wait (bounded) for every copy this CTA may still have in flight
+    if (threadIdx.x == 0) {
+      atomicExch(&b.st->err, -5);  // RTCUR_ETIMEOUT
+#pragma unroll
+      for (int s2 = 0; s2 < kStages; ++s2) {
+        // the newest copy on stage s2 completes phase number issued-1 (parity (issued-1) & 1)
+        if (issued[s2] > seen[s2]) mbar_wait_bounded(&full[s2], (unsigned)((issued[s2] - 1) & 1));
+      }
+    }
+    __syncthreads();
+  }
+  (void)tile_bytes_full;
+  double* part = b.red + (size_t)TK_DENSE * kMaxRedBlocks * RT_RED_SLOTS;
+  const int bid = blockIdx.x;
+  double t0 = block_sum_d((double)res, sh);
+  if (threadIdx.x == 0) part[bid * RT_RED_SLOTS + 0] = t0;
+  t0 = block_sum_d((double)nnz, sh);
+  if (threadIdx.x == 0) part[bid * RT_RED_SLOTS + 1] = t0;
+  t0 = block_sum_d((double)inb, sh);
+  if (threadIdx.x == 0) part[bid * RT_RED_SLOTS + 2] = t0;
+  if (last_block_arrive(b.ticket + TK_DENSE)) {
+    State* w = b.st;
+    for (int slot = 0; slot < 3; ++slot) {
+      double acc = 0.0;
+      for (unsigned i2 = threadIdx.x; i2 < gridDim.x; i2 += blockDim.x) acc += part[i2 * RT_RED_SLOTS + slot];
+      acc = block_sum_d(acc, sh);
+      if (threadIdx.x == 0) {
+        if (slot == 0) w->resid_f = acc;
+        if (slot == 1) w->nnz_f = (long long)acc;
+        if (slot == 2) w->inband_f = (long long)acc;
+      }
+    }
+    if (threadIdx.x == 0) b.ticket[TK_DENSE] = 0u;
+  }
+}
+
+template <int RN>
+cudaError_t launch_tma_rn(const Geom& g, const Bufs& b, int tr, size_t smem, int grid, int threads,
+                          cudaStream_t s) {
+  k_dense_tma<RN><<<grid, threads, smem, s>>>(g, b, tr);
+  return cudaGetLastError();
+}
+
+template <int RN>
+cudaError_t prepare_tma_rn(size_t smem) {
+  return cudaFuncSetAttribute(k_dense_tma<RN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+// Tile geometry of the TMA pass; returns false when the pass does not apply (d_n % 4 != 0,
+// d_n > 4096, r_n > 8).
+bool tma_geometry(const Geom& g, int& tr, size_t& smem, int& threads) {
+  const long long dn = g.d[g.n - 1];
+  if (dn % 4 != 0 || dn > 4096 || g.rlast > 8) return false;
+  long long t = 32768 / (dn * 4);
+  if (t < 1) t = 1;
+  if (t > g.rowsT) t = g.rowsT;
+  tr = (int)t;
+  smem = (size_t)kStages * (tr * dn * 4 + (((tr * g.rlast + 3) & ~3) + 4) * 4);
+  threads = (int)(((dn / 4 + 31) / 32) * 32);
+  return true;
+}
+
+// L_out = L^(k) (copy k & 1); S_out = HT_{zeta^(k)}(X - L^(k-1)) (copy (k-1) & 1), zero if k = 0.
+// Rows of d_n floats; a block strides over rows, each thread owns one column.
+__global__ void __launch_bounds__(256) k_materialize(Geom g, Bufs b, float* L_out, float* S_out) {
+  const State* st = b.st;
+  const int k = st->k;
+  const int cur = k & 1, prv = (k + 1) & 1;
+  const float zf = (float)st->zeta;
+  const float* X = b.sp->X;
+  const int rn = g.rlast;
+  const long long dn = g.d[g.n - 1];
+  const long long col = (long long)blockIdx.y * blockDim.x + threadIdx.x;
+  if (col >= dn) return;
+  const float* Tc = b.T[cur];
+  const float* Tp = b.T[prv];
+  float bc[RT_MAXR], bp[RT_MAXR];
+#pragma unroll
+  for (int c = 0; c < RT_MAXR; ++c) {
+    bc[c] = (c < rn) ? b.B[cur][g.offB[g.n - 1] + col * rn + c] : 0.f;
+    bp[c] = (c < rn) ? b.B[prv][g.offB[g.n - 1] + col * rn + c] : 0.f;
+  }
+#pragma unroll 8
+  for (long long r = blockIdx.x; r < g.rowsT; r += gridDim.x) {
+    const long long e = r * dn + col;
+    if (L_out) {
+      float L = 0.f;
+#pragma unroll
+      for (int c = 0; c < RT_MAXR; ++c)
+        if (c < rn) L = fmaf(__ldg(Tc + r * rn + c), bc[c], L);
+      __stcs(L_out + e, (k == 0) ? 0.f : L);
+    }
+    if (S_out) {
+      float sv = 0.f;
+      if (k > 0) {
+        float L = 0.f;
+#pragma unroll
+        for (int c = 0; c < RT_MAXR; ++c)
+          if (c < rn) L = fmaf(__ldg(Tp + r * rn + c), bp[c], L);
+        float dl = __ldcs(X + e) - L;
+        sv = (fabsf(dl) > zf) ? dl : 0.f;
+      }
+      __stcs(S_out + e, sv);
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t prepare_dense(const Geom& g) {
+  int tr, threads;
+  size_t smem;
+  if (!tma_geometry(g, tr, smem, threads)) return cudaSuccess;
+  switch (g.rlast) {
+    case 1: return prepare_tma_rn<1>(smem);
+    case 2: return prepare_tma_rn<2>(smem);
+    case 3: return prepare_tma_rn<3>(smem);
+    case 4: return prepare_tma_rn<4>(smem);
+    case 5: return prepare_tma_rn<5>(smem);
+    case 6: return prepare_tma_rn<6>(smem);
+    case 7: return prepare_tma_rn<7>(smem);
+    default: return prepare_tma_rn<8>(smem);
+  }
+}
+
+cudaError_t launch_dense(const Geom& g, const Bufs& b, int form, cudaStream_t s) {
+  if (form != 0) return cudaErrorNotSupported;
+  {
+    int tr, threads;
+    size_t smem;
+    if (tma_geometry(g, tr, smem, threads)) {
+      long long ntiles = (g.rowsT + tr - 1) / tr;
+      int grid = (int)(ntiles < 144 ? ntiles : 144);
+      switch (g.rlast) {
+        case 1: return launch_tma_rn<1>(g, b, tr, smem, grid, threads, s);
+        case 2: return launch_tma_rn<2>(g, b, tr, smem, grid, threads, s);
+        case 3: return launch_tma_rn<3>(g, b, tr, smem, grid, threads, s);
+        case 4: return launch_tma_rn<4>(g, b, tr, smem, grid, threads, s);
+        case 5: return launch_tma_rn<5>(g, b, tr, smem, grid, threads, s);
+        case 6: return launch_tma_rn<6>(g, b, tr, smem, grid, threads, s);
+        case 7: return launch_tma_rn<7>(g, b, tr, smem, grid, threads, s);
+        default: return launch_tma_rn<8>(g, b, tr, smem, grid, threads, s);
+      }
+    }
+  }
+  const long long dn = g.d[g.n - 1];
+  const bool vec = (dn % 4) == 0;
+  const long long cols = vec ? dn / 4 : dn;
+  int bx = (int)(((cols + 31) / 32) * 32);
+  if (bx > 512) bx = 512;
+  int gy = (int)((cols + bx - 1) / bx);
+  // about four blocks of bx threads per SM, capped by the reduction slots
+  long long gx = (152LL * 4 * 256) / bx;
+  if (gx * gy > kMaxRedBlocks) gx = kMaxRedBlocks / gy;
+  if (gx < 1) gx = 1;
+  if (gx > g.rowsT) gx = g.rowsT;
+  dim3 grid((unsigned)gx, (unsigned)gy);
+  if (vec)
+    k_dense_fp32<true><<<grid, bx, 0, s>>>(g, b);
+  else
+    k_dense_fp32<false><<<grid, bx, 0, s>>>(g, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_materialize(const Geom& g, const Bufs& b, float* L_out, float* S_out,
+                               cudaStream_t s) {
+  if (!L_out && !S_out) return cudaSuccess;
+  const long long dn = g.d[g.n - 1];
+  int bx = (int)(dn < 256 ? ((dn + 31) / 32) * 32 : 256);
+  unsigned gy = (unsigned)((dn + bx - 1) / bx);
+  long long gx = (152LL * 8 * 256) / (bx * (long long)gy);
+  if (gx < 1) gx = 1;
+  if (gx > g.rowsT) gx = g.rowsT;
+  k_materialize<<<dim3((unsigned)gx, gy), bx, 0, s>>>(g, b, L_out, S_out);
+  return cudaGetLastError();
+}

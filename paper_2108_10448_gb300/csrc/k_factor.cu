@@ -1,0 +1,200 @@
+// Factor formation: the new L^(k+1) of Eq. (L=CUR) in Tucker form G x_i B_i.
+//
+// With W_i = C_i(I_i,:) = Q Sigma V^T and its rank-r truncation, C_i U_i^+ = C_i V_r Sigma_r^-1
+// Q_r^T = B_i Q_r^T, so
+//   L = R x_i (C_i U_i^+) = (R x_i Q_{r,i}^T) x_i B_i = G x_i B_i,
+//   B_i = C_i Y_i with Y_i = V_r Sigma_r^-1 (d_i x r_i),   G = R x_1 Q_1^T ... x_n Q_n^T.
+// The evaluation table T = G x_1 B_1 ... x_{n-1} B_{n-1} (prod_{i<n} d_i rows, r_n columns) is
+// what every later L evaluation reads (see rtcur_internal.cuh).
+#include "rtcur_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 128;
+constexpr int kChunk = 32;   // b-columns per split-K partial of B_i = C_i Y_i
+
+// B partials: block -> (mode, t-block, chunk); thread -> row t.
+__global__ void __launch_bounds__(kThreads) k_factor_B_partial(Geom g, Bufs b) {
+  int blk = blockIdx.x, i = 0;
+  int tblocks = 0, chunks = 0;
+  for (; i < g.n; ++i) {
+    tblocks = (int)((g.d[i] + kThreads - 1) / kThreads);
+    chunks = (g.q[i] + kChunk - 1) / kChunk;
+    if (blk < tblocks * chunks) break;
+    blk -= tblocks * chunks;
+  }
+  if (i >= g.n) return;
+  const int ch = blk / tblocks;
+  const long long t = (long long)(blk % tblocks) * kThreads + threadIdx.x;
+  if (t >= g.d[i]) return;
+  const int r = g.r[i];
+  const int b0 = ch * kChunk, b1 = min(g.q[i], b0 + kChunk);
+  const float* C = b.XS + g.seg[i + 1];
+  const double* Y = b.Y + g.offY[i];
+  double acc[RT_MAXR];
+#pragma unroll
+  for (int c = 0; c < RT_MAXR; ++c) acc[c] = 0.0;
+  for (int bc = b0; bc < b1; ++bc) {
+    double x = (double)C[(long long)bc * g.d[i] + t];
+#pragma unroll
+    for (int c = 0; c < RT_MAXR; ++c)
+      if (c < r) acc[c] = fma(x, Y[(long long)bc * r + c], acc[c]);
+  }
+  double* out = b.Bpart + (long long)ch * g.sumB + g.offB[i] + t * r;
+#pragma unroll
+  for (int c = 0; c < RT_MAXR; ++c)
+    if (c < r) out[c] = acc[c];
+}
+
+// B_next = sum of the partials in chunk order (deterministic), rounded to FP32.
+__global__ void __launch_bounds__(kThreads) k_factor_B_reduce(Geom g, Bufs b) {
+  long long e = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (e >= g.sumB) return;
+  int i = 0;
+  while (i + 1 < g.n && e >= g.offB[i + 1]) ++i;
+  const int chunks = (g.q[i] + kChunk - 1) / kChunk;
+  double acc = 0.0;
+  for (int ch = 0; ch < chunks; ++ch) acc += b.Bpart[(long long)ch * g.sumB + e];
+  b.B[(b.st->k + 1) & 1][e] = (float)acc;
+}
+
+// One stage of G = R x_{n-1} Q^T ... x_0 Q^T (modes contracted from last to first).
+// Before stage s the modes j' > j = n-1-s already have size r, the others m. Q_j (m_j x r_j,
+// FP64) is staged in shared memory; each thread forms one output as an FP64 dot product.
+__global__ void __launch_bounds__(kThreads) k_core_stage(Geom g, Bufs b, int s, long long nout) {
+  __shared__ double Qs[RT_MAXM * RT_MAXR];
+  const int n = g.n;
+  const int j = n - 1 - s;
+  const int r = g.r[j];
+  const int mj = g.m[j];
+  const double* Q = b.Qr + g.offQ[j];
+  for (int t = threadIdx.x; t < mj * r; t += blockDim.x) Qs[t] = Q[t];
+  __syncthreads();
+  long long o = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (o >= nout) return;
+  int shp_in[RT_MAXN], shp_out[RT_MAXN];
+  for (int l = 0; l < n; ++l) {
+    shp_in[l] = (l > j) ? g.r[l] : g.m[l];
+    shp_out[l] = (l >= j) ? g.r[l] : g.m[l];
+  }
+  int co[RT_MAXN];
+  long long rem = o;
+  for (int l = n - 1; l >= 0; --l) {
+    co[l] = (int)(rem % shp_out[l]);
+    rem /= shp_out[l];
+  }
+  long long base = 0, strj = 1;
+  {
+    long long st = 1;
+    for (int l = n - 1; l >= 0; --l) {
+      if (l == j) strj = st;
+      else base += (long long)co[l] * st;
+      st *= shp_in[l];
+    }
+  }
+  const int cj = co[j];
+  double acc = 0.0;
+  if (s == 0) {
+    const float* R = b.XS;  // segment 0
+    for (int a = 0; a < mj; ++a) acc = fma((double)R[base + a * strj], Qs[a * r + cj], acc);
+  } else {
+    const double* Zin = b.Z[(s - 1) & 1];
+    for (int a = 0; a < mj; ++a) acc = fma(Zin[base + a * strj], Qs[a * r + cj], acc);
+  }
+  if (s == n - 1) {
+    b.G[(b.st->k + 1) & 1][o] = (float)acc;
+  } else {
+    b.Z[s & 1][o] = acc;
+  }
+}
+
+// Table stage A: H[c_0, p_1..p_{n-2}, c_{n-1}] = sum over c_1..c_{n-2} of
+// G[c_0, c_1, .., c_{n-1}] prod_l B_l[p_l, c_l]   (H = G when n = 2).
+__global__ void __launch_bounds__(kThreads) k_table_A(Geom g, Bufs b, int next) {
+  long long o = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (o >= g.nH) return;
+  const int n = g.n;
+  const int cp = next ? ((b.st->k + 1) & 1) : (b.st->k & 1);
+  const float* G = b.G[cp];
+  const float* B = b.B[cp];
+  // decode o over (r_0, d_1, ..., d_{n-2}, r_{n-1})
+  long long rem = o;
+  const int cl = (int)(rem % g.r[n - 1]);
+  rem /= g.r[n - 1];
+  long long p[RT_MAXN];
+  for (int l = n - 2; l >= 1; --l) {
+    p[l] = rem % g.d[l];
+    rem /= g.d[l];
+  }
+  const int c0 = (int)rem;
+  // iterate over the middle core indices c_1..c_{n-2}
+  int ncomb = 1;
+  for (int l = 1; l <= n - 2; ++l) ncomb *= g.r[l];
+  double acc = 0.0;
+  for (int t = 0; t < ncomb; ++t) {
+    int tr = t;
+    double prod = 1.0;
+    long long gidx = 0;
+    int cmid[RT_MAXN];
+    for (int l = n - 2; l >= 1; --l) {
+      cmid[l] = tr % g.r[l];
+      tr /= g.r[l];
+    }
+    gidx = c0;
+    for (int l = 1; l <= n - 2; ++l) {
+      gidx = gidx * g.r[l] + cmid[l];
+      prod *= (double)B[g.offB[l] + p[l] * g.r[l] + cmid[l]];
+    }
+    gidx = gidx * g.r[n - 1] + cl;
+    acc = fma((double)G[gidx], prod, acc);
+  }
+  b.H[o] = (float)acc;
+}
+
+// Table stage B: T[p_0, rest] = sum_{c_0} B_0[p_0, c_0] H[c_0, rest], FP32 FMA in ascending c_0.
+__global__ void __launch_bounds__(kThreads) k_table_B(Geom g, Bufs b, int next) {
+  const long long rest = g.nH / g.r[0];
+  long long o = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (o >= g.d[0] * rest) return;
+  const int cp = next ? ((b.st->k + 1) & 1) : (b.st->k & 1);
+  const float* B0 = b.B[cp];
+  const long long p0 = o / rest, w = o - p0 * rest;
+  float acc = 0.f;
+  for (int c = 0; c < g.r[0]; ++c) acc = fmaf(B0[p0 * g.r[0] + c], b.H[c * rest + w], acc);
+  b.T[cp][o] = acc;
+}
+
+inline int nblocks(long long work) { return (int)((work + kThreads - 1) / kThreads); }
+
+}  // namespace
+
+cudaError_t launch_factor_B(const Geom& g, const Bufs& b, cudaStream_t s) {
+  int blocks = 0;
+  for (int i = 0; i < g.n; ++i)
+    blocks += (int)((g.d[i] + kThreads - 1) / kThreads) * ((g.q[i] + kChunk - 1) / kChunk);
+  k_factor_B_partial<<<blocks, kThreads, 0, s>>>(g, b);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_factor_B_reduce<<<nblocks(g.sumB), kThreads, 0, s>>>(g, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_core(const Geom& g, const Bufs& b, cudaStream_t s) {
+  for (int st = 0; st < g.n; ++st) {
+    int j = g.n - 1 - st;
+    long long nout = 1;
+    for (int l = 0; l < g.n; ++l) nout *= (l >= j) ? g.r[l] : g.m[l];
+    k_core_stage<<<nblocks(nout), kThreads, 0, s>>>(g, b, st, nout);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_table(const Geom& g, const Bufs& b, int next, cudaStream_t s) {
+  k_table_A<<<nblocks(g.nH), kThreads, 0, s>>>(g, b, next);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_table_B<<<nblocks(g.rowsT * g.rlast), kThreads, 0, s>>>(g, b, next);
+  return cudaGetLastError();
+}

@@ -1,0 +1,1108 @@
+// Truncated pseudoinverse of U_i = C_i(I_i, :) (Eq. (R, C_i, U_i): U_i = SVD_{r_i}(W_i),
+// W_i = C_i(I_i, :), an m_i x q_i matrix), computed in FP64 as the top-r_i eigenpairs of the
+// Gram matrix M_i = W_i W_i^T:  W_r^+ = V_r Sigma_r^-1 Q_r^T with V_r Sigma_r = W^T Q_r.
+//
+// GB300 runs FP64 at 1/58 of its FP32 rate, so the FP64 work is kept GEMM-shaped and spread
+// over many SMs, and the sequential part runs in FP32:
+//   1. k_gram    M_i in FP64 (FP32 products are exact in FP64), 8x8 output tiles over the grid.
+//   2. k_jacobi  FP32 cyclic Jacobi on fl32(M_i), round-robin pair ordering (parallel Jacobi,
+//                Brent and Luk 1985), one CTA per mode, matrix and vectors in shared memory.
+//                Gives an FP32-accurate full eigenbasis Xh and eigenvalues lam.
+//   3. k_refine  FP64 refinement of the top-r subspace by the Ogita-Aishima iteration
+//                (Ogita and Aishima 2018, "Iterative refinement for symmetric eigenvalue
+//                decomposition"), restricted to the top block against the tail (pairs inside the
+//                top block or inside the tail are not rotated; their first-order term is the
+//                orthogonality correction only). Each step roughly squares the subspace error;
+//                two steps take the FP32 basis to FP64 accuracy. Then an FP64 Rayleigh-Ritz on
+//                the r x r block, the cutoff of SVD_r, and Y_i = V_r Sigma_r^-1 = W^T Q_r
+//                Sigma_r^-2. One thread-block cluster of RT_CLUSTER CTAs per mode shares the
+//                m x r panels through global memory (L2) between cluster barriers.
+#include <cooperative_groups.h>
+
+#include "rtcur_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace {
+
+constexpr int kGramTile = 8;
+constexpr int kGramChunk = 512;
+constexpr int kJacThreads = 1024;
+constexpr int kRefThreads = 256;
+
+__device__ __forceinline__ float w_entry(const Geom& g, const Bufs& b, const long long* set, int i,
+                                         int a, int bcol) {
+  // W_i[a, b] = C_i[I_i[a], b], kept compact (m_i x q_i, row-major) by the sampled threshold
+  (void)set;
+  return b.W[g.offW[i] + (long long)a * g.q[i] + bcol];
+}
+
+__device__ __forceinline__ const long long* set_of(const Geom& g, const Bufs& b) {
+  long long s = (g.variant == 1) ? (long long)(b.st->k % g.n_sets) : 0;
+  return b.idx + s * g.set_len;
+}
+
+// ------------------------------------------------------------------ 1. FP64 Gram matrix
+__global__ void __launch_bounds__(kGramTile * kGramTile) k_gram(Geom g, Bufs b) {
+  __shared__ float wa[kGramTile][kGramChunk + 1];
+  __shared__ float wb[kGramTile][kGramChunk + 1];
+  // locate (mode, tile) for this block: per mode nt(nt+1)/2 lower-triangle tiles
+  int blk = blockIdx.x, i = 0, nt = 0;
+  for (; i < g.n; ++i) {
+    nt = (g.m[i] + kGramTile - 1) / kGramTile;
+    int cnt = nt * (nt + 1) / 2;
+    if (blk < cnt) break;
+    blk -= cnt;
+  }
+  if (i >= g.n) return;
+  int ta = 0;
+  while ((ta + 1) * (ta + 2) / 2 <= blk) ++ta;
+  int tb = blk - ta * (ta + 1) / 2;  // tb <= ta
+  const long long* set = set_of(g, b);
+  const int m = g.m[i], q = g.q[i];
+  const int ty = threadIdx.x / kGramTile, tx = threadIdx.x % kGramTile;
+  const int a0 = ta * kGramTile, b0 = tb * kGramTile;
+  double acc = 0.0;
+  for (int c0 = 0; c0 < q; c0 += kGramChunk) {
+    int cn = min(kGramChunk, q - c0);
+    for (int e = threadIdx.x; e < kGramTile * cn; e += blockDim.x) {
+      int rr = e / cn, cc = e % cn;
+      wa[rr][cc] = (a0 + rr < m) ? w_entry(g, b, set, i, a0 + rr, c0 + cc) : 0.f;
+      wb[rr][cc] = (b0 + rr < m) ? w_entry(g, b, set, i, b0 + rr, c0 + cc) : 0.f;
+    }
+    __syncthreads();
+    for (int cc = 0; cc < cn; ++cc) acc = fma((double)wa[ty][cc], (double)wb[tx][cc], acc);
+    __syncthreads();
+  }
+  int ra = a0 + ty, rb = b0 + tx;
+  if (ra < m && rb < m) {
+    double* M = b.gram + g.offM[i];
+    M[(long long)ra * m + rb] = acc;
+    M[(long long)rb * m + ra] = acc;
+  }
+}
+
+// ------------------------------------------------------------------ 2. FP32 Jacobi
+__device__ __forceinline__ int pk(int r, int c, int N) {
+  if (r > c) { int t = r; r = c; c = t; }
+  return r * N - (r * (r - 1)) / 2 + (c - r);
+}
+
+__device__ __forceinline__ void tri_decode(int w, int P, int& a, int& bb) {
+  float tp = 2.f * P + 1.f;
+  float fa = (tp - sqrtf(fmaxf(tp * tp - 8.f * (float)w, 0.f))) * 0.5f;
+  int aa = max(0, min(P - 1, (int)fa));
+  while (aa > 0 && aa * P - (aa * (aa - 1)) / 2 > w) --aa;
+  while (aa + 1 < P && (aa + 1) * P - ((aa + 1) * aa) / 2 <= w) ++aa;
+  a = aa;
+  bb = aa + (w - (aa * P - (aa * (aa - 1)) / 2));
+}
+
+__global__ void __launch_bounds__(kJacThreads) k_jacobi(Geom g, Bufs b) {
+  extern __shared__ float smem[];
+  __shared__ int nrot;
+  __shared__ float tabs;
+  const int i = blockIdx.x;
+  const int m = g.m[i];
+  const int N = m + (m & 1);
+  const int P = N / 2;
+  const int Vs = N + 1;
+  float* Mp = smem;                              // packed upper triangle, N(N+1)/2
+  float* V = Mp + (N * (N + 1)) / 2;             // m x Vs
+  int* pp = reinterpret_cast<int*>(V + m * Vs);  // P
+  int* pq = pp + P;
+  float* pc = reinterpret_cast<float*>(pq + P);
+  float* ps = pc + P;
+  float* pt = ps + P;
+  const int tid = threadIdx.x;
+  const double* M64 = b.gram + g.offM[i];
+  for (int t = tid; t < N * N; t += blockDim.x) {
+    int r = t / N, c = t % N;
+    if (r <= c) Mp[pk(r, c, N)] = (c < m) ? (float)M64[(long long)r * m + c] : 0.f;
+  }
+  for (int t = tid; t < m * Vs; t += blockDim.x) {
+    int r = t / Vs, c = t % Vs;
+    V[t] = (r == c) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  const float tol = 4.f * 5.9604645e-8f;  // 4 * 2^-24
+  const int nblk = (P * (P + 1)) / 2;
+  for (int sw = 0; sw < g.max_sweeps; ++sw) {
+    if (tid == 0) {
+      nrot = 0;
+      float mx = 0.f;
+      for (int j = 0; j < m; ++j) mx = fmaxf(mx, Mp[pk(j, j, N)]);
+      tabs = 5.9604645e-8f * mx;
+    }
+    __syncthreads();
+    for (int rd = 0; rd < N - 1; ++rd) {
+      if (tid < P) {
+        int k = tid;
+        int x = (k == 0) ? 0 : ((k - 1 + rd) % (N - 1)) + 1;
+        int y = ((N - 1 - k - 1 + rd) % (N - 1)) + 1;
+        int p = min(x, y), q = max(x, y);
+        float c = 1.f, s = 0.f, tt = 0.f;
+        if (q < m) {
+          float app = Mp[pk(p, p, N)], aqq = Mp[pk(q, q, N)], apq = Mp[pk(p, q, N)];
+          if (fabsf(apq) > tol * sqrtf(fabsf(app * aqq)) && fabsf(apq) > tabs) {
+            float theta = (aqq - app) / (2.f * apq);
+            tt = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
+            c = 1.f / sqrtf(tt * tt + 1.f);
+            s = tt * c;
+            atomicAdd(&nrot, 1);
+          }
+        }
+        pp[k] = p; pq[k] = q; pc[k] = c; ps[k] = s; pt[k] = tt;
+      }
+      __syncthreads();
+      for (int w = tid; w < nblk + m * P; w += blockDim.x) {
+        if (w < nblk) {
+          int a, bb;
+          tri_decode(w, P, a, bb);
+          float s1 = ps[a], s2 = ps[bb];
+          if (s1 == 0.f && s2 == 0.f) continue;
+          if (a == bb) {
+            int p = pp[a], q = pq[a];
+            float apq = Mp[pk(p, q, N)];
+            float tt = pt[a];
+            Mp[pk(p, p, N)] -= tt * apq;
+            Mp[pk(q, q, N)] += tt * apq;
+            Mp[pk(p, q, N)] = 0.f;
+          } else {
+            int p1 = pp[a], q1 = pq[a], p2 = pp[bb], q2 = pq[bb];
+            float c1 = pc[a], c2 = pc[bb];
+            int i00 = pk(p1, p2, N), i01 = pk(p1, q2, N), i10 = pk(q1, p2, N), i11 = pk(q1, q2, N);
+            float x00 = Mp[i00], x01 = Mp[i01], x10 = Mp[i10], x11 = Mp[i11];
+            float r00 = c1 * x00 - s1 * x10, r01 = c1 * x01 - s1 * x11;
+            float r10 = s1 * x00 + c1 * x10, r11 = s1 * x01 + c1 * x11;
+            Mp[i00] = c2 * r00 - s2 * r01;
+            Mp[i01] = s2 * r00 + c2 * r01;
+            Mp[i10] = c2 * r10 - s2 * r11;
+            Mp[i11] = s2 * r10 + c2 * r11;
+          }
+        } else {
+          int item = w - nblk;
+          int k = item / m, a = item - k * m;
+          float s = ps[k];
+          if (s == 0.f) continue;
+          float c = pc[k];
+          float* row = V + a * Vs;
+          float vp = row[pp[k]], vq = row[pq[k]];
+          row[pp[k]] = c * vp - s * vq;
+          row[pq[k]] = s * vp + c * vq;
+        }
+      }
+      __syncthreads();
+    }
+    int done = (nrot == 0);
+    __syncthreads();
+    if (done) break;
+  }
+  float* outV = b.jV + g.offM[i];
+  for (int t = tid; t < m * m; t += blockDim.x) {
+    int r = t / m, c = t % m;
+    outV[t] = V[r * Vs + c];
+  }
+  for (int j = tid; j < m; j += blockDim.x) b.jL[g.offL[i] + j] = Mp[pk(j, j, N)];
+}
+
+// Fast path for m <= 128: full (both triangles) storage so every 2x2 block (pair a, pair b) is
+// updated by its own thread with plain row/column addressing, and block/vector-row ownership is
+// fixed for the whole launch. With `warm` set (k >= 1) the basis of the previous iteration
+// starts the sweep: M <- V0^T M V0 and V <- V0, so the rotations only have to follow the change
+// of M between iterations.
+constexpr int kFullMaxN = 128;
+constexpr int kFullLd = kFullMaxN + 1;
+
+__global__ void __launch_bounds__(kJacThreads, 1) k_jacobi_full(Geom g, Bufs b, int warm_ok) {
+  extern __shared__ float smem[];
+  __shared__ int nrot;
+  __shared__ float tabs;
+  __shared__ int pp[kFullMaxN / 2], pq[kFullMaxN / 2];
+  __shared__ float pc[kFullMaxN / 2], ps[kFullMaxN / 2], pt[kFullMaxN / 2];
+  const int i = blockIdx.x;
+  const int m = g.m[i];
+  const int N = m + (m & 1);
+  const int P = N / 2;
+  float* M = smem;                        // N x kFullLd
+  float* V = M + kFullMaxN * kFullLd;     // m x kFullLd (row a, column j = vector j)
+  float* Tm = V + kFullMaxN * kFullLd;    // scratch for the warm start
+  const int tid = threadIdx.x;
+  const double* M64 = b.gram + g.offM[i];
+  float* outV = b.jV + g.offM[i];
+  const bool warm = warm_ok && (b.st->k >= 1);
+  for (int t = tid; t < N * N; t += blockDim.x) {
+    int r = t / N, c = t - r * N;
+    M[r * kFullLd + c] = (r < m && c < m) ? (float)M64[(long long)r * m + c] : 0.f;
+  }
+  for (int t = tid; t < m * N; t += blockDim.x) {
+    int r = t / N, c = t - r * N;
+    V[r * kFullLd + c] = warm ? ((c < m) ? outV[(long long)r * m + c] : 0.f) : ((r == c) ? 1.f : 0.f);
+  }
+  __syncthreads();
+  if (warm) {  // M <- V^T M V in FP32 (two passes through the scratch panel)
+    for (int t = tid; t < m * m; t += blockDim.x) {
+      int r = t / m, c = t - r * m;
+      float acc = 0.f;
+      for (int u = 0; u < m; ++u) acc = fmaf(M[r * kFullLd + u], V[u * kFullLd + c], acc);
+      Tm[r * kFullLd + c] = acc;
+    }
+    __syncthreads();
+    for (int t = tid; t < m * m; t += blockDim.x) {
+      int r = t / m, c = t - r * m;
+      if (c < r) continue;
+      float acc = 0.f;
+      for (int u = 0; u < m; ++u) acc = fmaf(V[u * kFullLd + r], Tm[u * kFullLd + c], acc);
+      M[r * kFullLd + c] = acc;
+      M[c * kFullLd + r] = acc;
+    }
+    __syncthreads();
+  }
+  // fixed ownership: up to 4 blocks (P*P <= 4096) and 8 vector items (m*P <= 8192) per thread
+  int ba[4], bb[4], nb = 0;
+  for (int w = tid; w < P * P && nb < 4; w += blockDim.x, ++nb) { ba[nb] = w / P; bb[nb] = w - ba[nb] * P; }
+  int vk[8], vr[8], nv = 0;
+  for (int w = tid; w < m * P && nv < 8; w += blockDim.x, ++nv) { vk[nv] = w / m; vr[nv] = w - vk[nv] * m; }
+  const float tol = 4.f * 5.9604645e-8f;  // 4 * 2^-24
+  for (int sw = 0; sw < g.max_sweeps; ++sw) {
+    if (tid == 0) {
+      nrot = 0;
+      float mx = 0.f;
+      for (int j = 0; j < m; ++j) mx = fmaxf(mx, M[j * kFullLd + j]);
+      tabs = 5.9604645e-8f * mx;
+    }
+    __syncthreads();
+    for (int rd = 0; rd < N - 1; ++rd) {
+      if (tid < P) {
+        int k = tid;
+        int x = (k == 0) ? 0 : ((k - 1 + rd) % (N - 1)) + 1;
+        int y = ((N - 2 - k + rd) % (N - 1)) + 1;
+        int p = min(x, y), q = max(x, y);
+        float c = 1.f, s2 = 0.f, tt = 0.f;
+        if (q < m) {
+          float app = M[p * kFullLd + p], aqq = M[q * kFullLd + q], apq = M[p * kFullLd + q];
+          if (fabsf(apq) > tol * sqrtf(fabsf(app * aqq)) && fabsf(apq) > tabs) {
+            float theta = (aqq - app) / (2.f * apq);
+            tt = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
+            c = 1.f / sqrtf(tt * tt + 1.f);
+            s2 = tt * c;
+            atomicAdd(&nrot, 1);
+          }
+        }
+        pp[k] = p; pq[k] = q; pc[k] = c; ps[k] = s2; pt[k] = tt;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (u >= nb) break;
+        const int a = ba[u], c2i = bb[u];
+        const float s1 = ps[a], s2 = ps[c2i];
+        if (s1 == 0.f && s2 == 0.f) continue;
+        const int p1 = pp[a], q1 = pq[a];
+        if (a == c2i) {
+          float apq = M[p1 * kFullLd + q1];
+          float tt = pt[a];
+          M[p1 * kFullLd + p1] -= tt * apq;
+          M[q1 * kFullLd + q1] += tt * apq;
+          M[p1 * kFullLd + q1] = 0.f;
+          M[q1 * kFullLd + p1] = 0.f;
+        } else {
+          const int p2 = pp[c2i], q2 = pq[c2i];
+          const float c1 = pc[a], c2 = pc[c2i];
+          float* rp = M + p1 * kFullLd;
+          float* rq = M + q1 * kFullLd;
+          float x00 = rp[p2], x01 = rp[q2], x10 = rq[p2], x11 = rq[q2];
+          float r00 = c1 * x00 - s1 * x10, r01 = c1 * x01 - s1 * x11;
+          float r10 = s1 * x00 + c1 * x10, r11 = s1 * x01 + c1 * x11;
+          rp[p2] = c2 * r00 - s2 * r01;
+          rp[q2] = s2 * r00 + c2 * r01;
+          rq[p2] = c2 * r10 - s2 * r11;
+          rq[q2] = s2 * r10 + c2 * r11;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (u >= nv) break;
+        const int k = vk[u];
+        const float s2 = ps[k];
+        if (s2 == 0.f) continue;
+        const float c = pc[k];
+        float* row = V + vr[u] * kFullLd;
+        const int p = pp[k], q = pq[k];
+        float vp = row[p], vq = row[q];
+        row[p] = c * vp - s2 * vq;
+        row[q] = s2 * vp + c * vq;
+      }
+      __syncthreads();
+    }
+    int done = (nrot == 0);
+    __syncthreads();
+    if (tid == 0) atomicMax(&b.st->jsweeps, sw + 1);
+    if (done) break;
+  }
+  for (int t = tid; t < m * m; t += blockDim.x) {
+    int r = t / m, c = t - r * m;
+    outV[t] = V[r * kFullLd + c];
+  }
+  for (int j = tid; j < m; j += blockDim.x) b.jL[g.offL[i] + j] = M[j * kFullLd + j];
+}
+
+// ------------------------------------------------------------------ 2b. FP32 tridiagonal eigensolver
+// For m <= 128 the FP32 eigenbasis comes from a tridiagonal reduction instead of Jacobi sweeps
+// (about m sequential steps instead of ~9 sweeps of m rounds):
+//   a. Householder tridiagonalisation Q^T M Q = T (Golub and Van Loan, Alg. 8.3.1), one warp per
+//      row for the symmetric matrix-vector product;
+//   b. all eigenvalues of T by multisection on Sturm counts (8 shifts per eigenvalue per round);
+//   c. eigenvectors of T by inverse iteration (tridiagonal LU with partial pivoting, three steps
+//      from a hashed start vector), except for the largest group of eigenvalues closer than
+//      1e-5 ||T|| (in practice the near-zero tail late in the solve), whose basis is taken as
+//      the orthogonal complement of all other vectors (Householder QR), and Gram-Schmidt inside
+//      any other small group;
+//   d. back-transformation by the stored reflectors, eight threads per column.
+// The result only has to be FP32-accurate: the FP64 refinement that follows fixes the top-r
+// subspace to FP64 accuracy.
+constexpr int kTriMax = 128;
+constexpr int kTriLd = kTriMax + 1;
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ int sturm_count(const float* d, const float* e2, int m, float x) {
+  int cnt = 0;
+  float q = d[0] - x;
+  if (q < 0.f) ++cnt;
+  for (int k = 1; k < m; ++k) {
+    if (q == 0.f) q = -1e-30f;
+    q = (d[k] - x) - e2[k - 1] / q;
+    if (q < 0.f) ++cnt;
+  }
+  return cnt;
+}
+
+// Solve (T - s I) y = y in place (FP32, tridiagonal LU with partial pivoting, as in LAPACK's
+// slagtf/slagts). Zero pivots are replaced by `pert`. Work arrays live in local memory.
+__device__ void tri_solve(const float* d, const float* e, int m, float s, float pert, float* y,
+                          int ystride) {
+  float l[kTriMax], dg[kTriMax], u1[kTriMax], u2[kTriMax];
+  unsigned char piv[kTriMax];
+  float cd = d[0] - s, cu1 = (m > 1) ? e[0] : 0.f, cu2 = 0.f;
+  for (int k = 0; k < m - 1; ++k) {
+    float sub = e[k];
+    float nd = d[k + 1] - s;
+    float nu = (k + 1 < m - 1) ? e[k + 1] : 0.f;
+    if (fabsf(cd) >= fabsf(sub)) {
+      piv[k] = 0;
+      if (cd == 0.f) cd = pert;
+      l[k] = sub / cd;
+      dg[k] = cd; u1[k] = cu1; u2[k] = cu2;
+      cd = nd - l[k] * cu1;
+      cu1 = nu;
+      cu2 = 0.f;
+    } else {
+      piv[k] = 1;
+      l[k] = cd / sub;
+      dg[k] = sub; u1[k] = nd; u2[k] = nu;
+      float ncd = cu1 - l[k] * nd;
+      cu1 = cu2 - l[k] * nu;
+      cd = ncd;
+      cu2 = 0.f;
+    }
+  }
+  if (cd == 0.f) cd = pert;
+  dg[m - 1] = cd;
+  for (int k = 0; k < m - 1; ++k) {
+    float a = y[k * ystride], bb = y[(k + 1) * ystride];
+    if (piv[k]) { float t = a; a = bb; bb = t; }
+    y[k * ystride] = a;
+    y[(k + 1) * ystride] = bb - l[k] * a;
+  }
+  float x1 = 0.f, x2 = 0.f;
+  for (int k = m - 1; k >= 0; --k) {
+    float t = y[k * ystride];
+    if (k + 1 < m) t -= u1[k] * x1;
+    if (k + 2 < m) t -= u2[k] * x2;
+    float xk = t / dg[k];
+    y[k * ystride] = xk;
+    x2 = x1;
+    x1 = xk;
+  }
+}
+
+__device__ __forceinline__ float hash_unit(int i, int j) {
+  unsigned h = (unsigned)j * 2654435761u + (unsigned)i * 40503u + 12345u;
+  h ^= h >> 16;
+  h *= 0x7feb352du;
+  h ^= h >> 15;
+  return (float)(h & 0xffffffu) * (1.f / 16777216.f) - 0.5f;
+}
+
+__global__ void __launch_bounds__(kJacThreads, 1) k_eig_tri(Geom g, Bufs b) {
+  extern __shared__ float smem[];
+  __shared__ float dv[kTriMax], ev[kTriMax], e2[kTriMax], tauv[kTriMax], vb[kTriMax], pv[kTriMax];
+  __shared__ float lam[kTriMax], qt[kTriMax];
+  __shared__ int cid[kTriMax], inbig[kTriMax], known[kTriMax];
+  __shared__ float sh_scale, sh_tau, sh_lo, sh_hi, sh_nrm;
+  __shared__ int sh_big, sh_nknown;
+  const int i = blockIdx.x;
+  const int m = g.m[i];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  float* A = smem;                       // m x kTriLd: matrix, then reflectors below the diagonal
+  float* Z = A + kTriMax * kTriLd;       // m x kTriLd: eigenvectors of T (columns)
+  float* Y = Z + kTriMax * kTriLd;       // m x kTriLd: QR work for the complement
+  const double* M64 = b.gram + g.offM[i];
+  long long tph = clock64();
+  for (int t = tid; t < m * m; t += blockDim.x) {
+    int r = t / m, c = t - r * m;
+    A[r * kTriLd + c] = (float)M64[t];
+  }
+  __syncthreads();
+  PHASE_MARK(tph, "tri.load");
+  // ---- a. tridiagonalisation
+  for (int j = 0; j + 2 < m; ++j) {
+    const int sN = m - j - 1;
+    if (wid == 0) {
+      float x0 = A[(j + 1) * kTriLd + j];
+      float acc = 0.f;
+      for (int k = 1 + lane; k < sN; k += 32) {
+        float x = A[(j + 1 + k) * kTriLd + j];
+        acc = fmaf(x, x, acc);
+      }
+      acc = warp_sum_f(acc);
+      if (lane == 0) {
+        if (acc == 0.f) {
+          sh_tau = 0.f; sh_scale = 0.f; ev[j] = x0;
+        } else {
+          float nrm = sqrtf(x0 * x0 + acc);
+          float beta = (x0 >= 0.f) ? -nrm : nrm;
+          sh_tau = (beta - x0) / beta;
+          sh_scale = 1.f / (x0 - beta);
+          ev[j] = beta;
+        }
+        dv[j] = A[j * kTriLd + j];
+        tauv[j] = sh_tau;
+      }
+    }
+    __syncthreads();
+    const float tau = sh_tau, scale = sh_scale;
+    for (int k = tid; k < sN; k += blockDim.x) {
+      float v = (k == 0) ? 1.f : A[(j + 1 + k) * kTriLd + j] * scale;
+      if (tau == 0.f) v = (k == 0) ? 1.f : 0.f;
+      vb[k] = v;
+    }
+    __syncthreads();
+    for (int k = tid; k < sN; k += blockDim.x) A[(j + 1 + k) * kTriLd + j] = vb[k];  // reflector
+    if (tau != 0.f) {
+      // p = tau * A22 v, one warp per row
+      for (int rr = wid; rr < sN; rr += nw) {
+        const float* row = A + (j + 1 + rr) * kTriLd + (j + 1);
+        float acc = 0.f;
+        for (int k = lane; k < sN; k += 32) acc = fmaf(row[k], vb[k], acc);
+        acc = warp_sum_f(acc);
+        if (lane == 0) pv[rr] = tau * acc;
+      }
+      __syncthreads();
+      // K = tau/2 * p.v (every warp, redundantly), then A22 -= v w^T + w v^T with w = p - K v
+      float acc = 0.f;
+      for (int k = lane; k < sN; k += 32) acc = fmaf(pv[k], vb[k], acc);
+      const float K = 0.5f * tau * warp_sum_f(acc);
+      for (int r = wid; r < sN; r += nw) {
+        const float vr = vb[r], wr = pv[r] - K * vr;
+        float* arow = A + (j + 1 + r) * kTriLd + (j + 1);
+        for (int c = lane; c < sN; c += 32) {
+          const float vc = vb[c], wc = pv[c] - K * vc;
+          arow[c] = arow[c] - vr * wc - wr * vc;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (m >= 2) {
+      dv[m - 2] = A[(m - 2) * kTriLd + (m - 2)];
+      ev[m - 2] = A[(m - 1) * kTriLd + (m - 2)];
+    }
+    dv[m - 1] = A[(m - 1) * kTriLd + (m - 1)];
+    float lo = 3.4e38f, hi = -3.4e38f, nrm = 0.f;
+    for (int k = 0; k < m; ++k) {
+      float rad = ((k > 0) ? fabsf(ev[k - 1]) : 0.f) + ((k + 1 < m) ? fabsf(ev[k]) : 0.f);
+      lo = fminf(lo, dv[k] - rad);
+      hi = fmaxf(hi, dv[k] + rad);
+      nrm = fmaxf(nrm, fabsf(dv[k]));
+      if (k + 1 < m) nrm = fmaxf(nrm, fabsf(ev[k]));
+      e2[k] = (k + 1 < m) ? ev[k] * ev[k] : 0.f;
+    }
+    float span = fmaxf(fabsf(lo), fabsf(hi));
+    sh_lo = lo - 1e-6f * span - 1e-30f;
+    sh_hi = hi + 1e-6f * span + 1e-30f;
+    sh_nrm = nrm + 1e-30f;
+  }
+  __syncthreads();
+  PHASE_MARK(tph, "tri.reduce");
+  // ---- b. multisection: group of 8 lanes per eigenvalue (ascending index ei)
+  {
+    const int G = 8;
+    const int ei = tid / G, gl = tid % G;
+    const unsigned gmask = 0xffu << ((lane / G) * G);
+    float a = sh_lo, bnd = sh_hi;
+    if (ei < m) {
+      for (int rd = 0; rd < 40; ++rd) {
+        // eigenvalues of the FP32 matrix are only determined to about eps ||T||
+        if (bnd - a <= 2.f * 5.9604645e-8f * (fmaxf(fabsf(a), fabsf(bnd)) + sh_nrm)) break;
+        float x = a + (bnd - a) * (float)(gl + 1) / (float)(G + 1);
+        int cnt = sturm_count(dv, e2, m, x);
+        float na = a, nb = bnd;
+        bool found = false;
+        for (int t = 0; t < G; ++t) {
+          float xt = __shfl_sync(gmask, x, (lane / G) * G + t);
+          int ct = __shfl_sync(gmask, cnt, (lane / G) * G + t);
+          if (!found) {
+            if (ct <= ei) na = xt;
+            else { nb = xt; found = true; }
+          }
+        }
+        a = na;
+        bnd = nb;
+      }
+      if (gl == 0) lam[ei] = 0.5f * (a + bnd);
+    } else {
+      // idle lanes of a partially used warp still take part in the shuffles above only if
+      // their group is active; groups with ei >= m skip the loop entirely (whole group).
+    }
+  }
+  __syncthreads();
+  PHASE_MARK(tph, "tri.bisect");
+  // ---- c. clusters, inverse iteration, complement
+  if (tid == 0) {
+    const float tol = 1e-5f * sh_nrm;
+    int c = 0, best = 0, bestsz = 1, cur = 1;
+    cid[0] = 0;
+    for (int k = 1; k < m; ++k) {
+      if (lam[k] - lam[k - 1] > tol) { ++c; cur = 1; }
+      else if (++cur > bestsz) { bestsz = cur; best = c; }
+      cid[k] = c;
+    }
+    sh_big = (bestsz >= 2) ? best : -1;
+    int nk = 0;
+    for (int k = 0; k < m; ++k) {
+      inbig[k] = (cid[k] == sh_big) ? 1 : 0;
+      if (!inbig[k]) known[nk++] = k;
+    }
+    sh_nknown = nk;
+  }
+  __syncthreads();
+  if (tid < m && !inbig[tid] && (tid == 0 || cid[tid] != cid[tid - 1])) {
+    // this thread owns its whole (non-big) cluster: members cstart..next start
+    const int c0 = tid;
+    int c1 = c0 + 1;
+    while (c1 < m && cid[c1] == cid[c0]) ++c1;
+    const float pert = 5.9604645e-8f * sh_nrm;
+    for (int k = c0; k < c1; ++k) {
+      float* y = Z + k;  // column k, stride kTriLd
+      for (int r = 0; r < m; ++r) y[r * kTriLd] = hash_unit(k, r);
+      for (int it = 0; it < 3; ++it) {
+        tri_solve(dv, ev, m, lam[k], pert, y, kTriLd);
+        for (int jj = c0; jj < k; ++jj) {  // Gram-Schmidt inside the cluster
+          float dot = 0.f;
+          for (int r = 0; r < m; ++r) dot = fmaf(Z[r * kTriLd + jj], y[r * kTriLd], dot);
+          for (int r = 0; r < m; ++r) y[r * kTriLd] -= dot * Z[r * kTriLd + jj];
+        }
+        float nn = 0.f;
+        for (int r = 0; r < m; ++r) nn = fmaf(y[r * kTriLd], y[r * kTriLd], nn);
+        float inv = (nn > 0.f) ? 1.f / sqrtf(nn) : 0.f;
+        for (int r = 0; r < m; ++r) y[r * kTriLd] *= inv;
+      }
+    }
+  }
+  __syncthreads();
+  PHASE_MARK(tph, "tri.inviter");
+  if (sh_big >= 0) {
+    // Householder QR of the known vectors (m x nk), then the complement H_1..H_nk [0; I]
+    const int nk = sh_nknown;
+    for (int t = tid; t < m * nk; t += blockDim.x) {
+      int r = t / nk, c = t - r * nk;
+      Y[r * kTriLd + c] = Z[r * kTriLd + known[c]];
+    }
+    __syncthreads();
+    for (int j = 0; j < nk; ++j) {
+      if (wid == 0) {
+        float acc = 0.f;
+        for (int r = j + lane; r < m; r += 32) acc = fmaf(Y[r * kTriLd + j], Y[r * kTriLd + j], acc);
+        acc = warp_sum_f(acc);
+        if (lane == 0) {
+          float x0 = Y[j * kTriLd + j];
+          float nx = sqrtf(acc);
+          float beta = (x0 >= 0.f) ? -nx : nx;
+          float v0 = x0 - beta;
+          float vn = acc - x0 * x0 + v0 * v0;
+          qt[j] = (vn > 0.f) ? 2.f / vn : 0.f;
+          vb[0] = v0;  // v = [v0, x(j+1:)]; kept in column j of Y with Y[j][j] = v0
+          Y[j * kTriLd + j] = v0;
+        }
+      }
+      __syncthreads();
+      const float t2 = qt[j];
+      for (int c = j + 1 + wid; c < nk; c += nw) {
+        float acc = 0.f;
+        for (int r = j + lane; r < m; r += 32) acc = fmaf(Y[r * kTriLd + j], Y[r * kTriLd + c], acc);
+        acc = warp_sum_f(acc) * t2;
+        for (int r = j + lane; r < m; r += 32) Y[r * kTriLd + c] -= acc * Y[r * kTriLd + j];
+      }
+      __syncthreads();
+    }
+    // complement columns: start from unit vectors e_{nk + cc}, apply H_nk..H_1 (reverse order)
+    int cc = 0;
+    for (int k = 0; k < m; ++k) {
+      if (!inbig[k]) continue;
+      for (int r = tid; r < m; r += blockDim.x) Z[r * kTriLd + k] = (r == nk + cc) ? 1.f : 0.f;
+      ++cc;
+    }
+    __syncthreads();
+    for (int j = nk - 1; j >= 0; --j) {
+      const float t2 = qt[j];
+      for (int k = wid; k < m; k += nw) {
+        if (!inbig[k]) continue;
+        float acc = 0.f;
+        for (int r = j + lane; r < m; r += 32) acc = fmaf(Y[r * kTriLd + j], Z[r * kTriLd + k], acc);
+        acc = warp_sum_f(acc) * t2;
+        for (int r = j + lane; r < m; r += 32) Z[r * kTriLd + k] -= acc * Y[r * kTriLd + j];
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  PHASE_MARK(tph, "tri.complement");
+  // ---- d. back-transformation Z <- H_0 ... H_{m-3} Z, eight threads per column
+  {
+    const int G = 8;
+    const int col = tid / G, gl = tid % G;
+    const unsigned gmask = 0xffu << ((lane / G) * G);
+    if (col < m) {
+      for (int j = m - 3; j >= 0; --j) {
+        const float tau = tauv[j];
+        if (tau == 0.f) continue;
+        float acc = 0.f;
+        for (int r = j + 1 + gl; r < m; r += G) acc = fmaf(A[r * kTriLd + j], Z[r * kTriLd + col], acc);
+        for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(gmask, acc, o);
+        acc *= tau;
+        for (int r = j + 1 + gl; r < m; r += G) Z[r * kTriLd + col] -= acc * A[r * kTriLd + j];
+      }
+    }
+  }
+  __syncthreads();
+  PHASE_MARK(tph, "tri.backtransform");
+  float* outV = b.jV + g.offM[i];
+  for (int t = tid; t < m * m; t += blockDim.x) {
+    int r = t / m, c = t - r * m;
+    outV[t] = Z[r * kTriLd + c];
+  }
+  for (int j = tid; j < m; j += blockDim.x) b.jL[g.offL[i] + j] = lam[j];
+  PHASE_MARK(tph, "tri.store");
+}
+
+// ------------------------------------------------------------------ 3. FP64 refinement
+__device__ void cluster_barrier() {
+  __threadfence();
+  cg::this_cluster().sync();
+}
+
+// Shared-memory layout of k_refine (doubles first): own rows of M, the full m x r panels X1, Yw
+// and E (re-read from global memory after each cluster barrier), the FP32 basis restricted to
+// this CTA's columns and rows, and a chunk of W columns for Y = W^T Q_r Sigma^-2.
+constexpr int kWChunk = 32;
+
+__host__ __device__ inline size_t refine_smem_bytes(int m, int r) {
+  int own = (m + RT_CLUSTER - 1) / RT_CLUSTER;
+  return sizeof(double) * ((size_t)own * m + 3 * (size_t)m * r) +
+         sizeof(float) * (2 * (size_t)own * m + (size_t)m * kWChunk);
+}
+
+__device__ __forceinline__ void load_panel(double* dst, const double* src, int n) {
+  for (int t = threadIdx.x; t < n; t += blockDim.x) dst[t] = src[t];
+}
+
+__global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b) {
+  extern __shared__ double rsm[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int crank = (int)cl.block_rank();
+  const int i = blockIdx.x / RT_CLUSTER;
+  const int m = g.m[i], r = g.r[i], q = g.q[i];
+  const int tid = threadIdx.x;
+  __shared__ int top[RT_MAXR];
+  __shared__ int pos_of[RT_MAXM];      // -1 for tail indices, else position in top
+  __shared__ double lamT[RT_MAXR];
+  __shared__ double Gq[RT_MAXR * RT_MAXR];
+  __shared__ double Hs[RT_MAXR * RT_MAXR];
+  __shared__ double Yh[RT_MAXR * RT_MAXR];
+  __shared__ double wv[RT_MAXR];
+  __shared__ int order[RT_MAXR];
+  __shared__ int tie;
+  __shared__ float lam[RT_MAXM];
+  for (int a = tid; a < m; a += blockDim.x) lam[a] = b.jL[g.offL[i] + a];
+  __syncthreads();
+  const float* Xh = b.jV + g.offM[i];               // m x m, column j = vector j
+  const double* M = b.gram + g.offM[i];
+  double* X1 = b.X1 + g.offQ[i];                    // m x r
+  double* Yw = b.ework + g.offQ[i];                 // m x r
+  double* E = b.ework + g.sumMR + g.offQ[i];        // m x r (rows: basis index)
+  double* Qw = b.ework + 2 * g.sumMR + g.offQ[i];   // m x r
+  double* Qr = b.Qr + g.offQ[i];
+  double* sig = b.sig + g.offR[i];
+  double* Yout = b.Y + g.offY[i];
+  const long long* set = set_of(g, b);
+  const int lo = (m * crank) / RT_CLUSTER, hi = (m * (crank + 1)) / RT_CLUSTER;
+  const int own = hi - lo;
+  const int ownmax = (m + RT_CLUSTER - 1) / RT_CLUSTER;
+  double* sM = rsm;                         // own x m
+  double* sX1 = sM + (size_t)ownmax * m;     // m x r
+  double* sYw = sX1 + (size_t)m * r;         // m x r
+  double* sE = sYw + (size_t)m * r;          // m x r
+  float* sXc = reinterpret_cast<float*>(sE + (size_t)m * r);  // m x own: Xh[a][lo + j]
+  float* sXr = sXc + (size_t)ownmax * m;     // own x m: Xh[lo + j][ii]
+  float* sW = sXr + (size_t)ownmax * m;      // m x kWChunk
+
+  long long tph = clock64();
+  if (tid == 0) {
+    tie = 0;
+    for (int a = 0; a < m; ++a) pos_of[a] = -1;
+    for (int j = 0; j < r; ++j) {  // r largest eigenvalues, descending; ties broken by index
+      int best = -1;
+      for (int a = 0; a < m; ++a)
+        if (pos_of[a] < 0 && (best < 0 || lam[a] > lam[best])) best = a;
+      top[j] = best;
+      pos_of[best] = j;
+    }
+  }
+  for (int t = tid; t < own * m; t += blockDim.x) {
+    int a = t / m, c = t - a * m;
+    sM[t] = M[(long long)(lo + a) * m + c];
+    sXr[t] = Xh[(long long)(lo + a) * m + c];
+  }
+  for (int t = tid; t < m * own; t += blockDim.x) {
+    int a = t / own, j = t - a * own;
+    sXc[t] = Xh[(long long)a * m + lo + j];
+  }
+  __syncthreads();
+  for (int t = tid; t < own * r; t += blockDim.x) {
+    int a = lo + t / r, j = t % r;
+    X1[(long long)a * r + j] = (double)Xh[(long long)a * m + top[j]];
+  }
+  cluster_barrier();
+  load_panel(sX1, X1, m * r);
+  __syncthreads();
+  PHASE_MARK(tph, "ref.init");
+  for (int step = 0; step < g.refine_steps; ++step) {
+    // S1: Yw = M X1 on own rows
+    for (int t = tid; t < own * r; t += blockDim.x) {
+      int a = t / r, j = t - a * r;
+      const double* Ma = sM + (size_t)a * m;
+      double acc = 0.0;
+      for (int c = 0; c < m; ++c) acc = fma(Ma[c], sX1[c * r + j], acc);
+      Yw[(long long)(lo + a) * r + j] = acc;
+    }
+    cluster_barrier();
+    load_panel(sYw, Yw, m * r);
+    __syncthreads();
+    // Rayleigh quotients of the current top columns (every CTA, redundantly)
+    if (tid < r) {
+      int j = tid;
+      double s1 = 0.0, nn = 0.0;
+      for (int a = 0; a < m; ++a) {
+        double x = sX1[a * r + j];
+        s1 = fma(x, sYw[a * r + j], s1);
+        nn = fma(x, x, nn);
+      }
+      lamT[j] = s1 / nn;
+    }
+    __syncthreads();
+    double lmax = lamT[0];
+    for (int j = 1; j < r; ++j) lmax = fmax(lmax, lamT[j]);
+    // S2: E for own basis indices ii; the basis is Xh with its top columns replaced by X1
+    for (int t = tid; t < own * r; t += blockDim.x) {
+      int jj = t / r, j = t - jj * r;
+      int ii = lo + jj;
+      int pi = pos_of[ii];
+      double s1 = 0.0, dot = 0.0;
+      if (pi >= 0) {
+        for (int a = 0; a < m; ++a) {
+          double xf = sX1[a * r + pi];
+          s1 = fma(xf, sYw[a * r + j], s1);
+          dot = fma(xf, sX1[a * r + j], dot);
+        }
+      } else {
+        for (int a = 0; a < m; ++a) {
+          double xf = (double)sXc[a * own + jj];
+          s1 = fma(xf, sYw[a * r + j], s1);
+          dot = fma(xf, sX1[a * r + j], dot);
+        }
+      }
+      double Rij = ((pi == j) ? 1.0 : 0.0) - dot;
+      double Eij;
+      if (pi >= 0) {
+        Eij = 0.5 * Rij;
+      } else {
+        double den = lamT[j] - (double)lam[ii];
+        if (fabs(den) > 1e-6 * fabs(lmax)) {
+          Eij = (s1 + lamT[j] * Rij) / den;
+        } else {
+          Eij = 0.5 * Rij;
+          tie = 1;
+        }
+      }
+      E[(long long)ii * r + j] = Eij;
+    }
+    cluster_barrier();
+    load_panel(sE, E, m * r);
+    __syncthreads();
+    // S3: X1 <- X1 + Xf E on own rows
+    for (int t = tid; t < own * r; t += blockDim.x) {
+      int a = t / r, j = t - a * r;
+      double upd = 0.0;
+      const float* xr = sXr + (size_t)a * m;
+      for (int ii = 0; ii < m; ++ii) {
+        int pi = pos_of[ii];
+        double xf = (pi >= 0) ? sX1[(lo + a) * r + pi] : (double)xr[ii];
+        upd = fma(xf, sE[ii * r + j], upd);
+      }
+      X1[(long long)(lo + a) * r + j] = sX1[(lo + a) * r + j] + upd;
+    }
+    cluster_barrier();
+    load_panel(sX1, X1, m * r);
+    __syncthreads();
+    PHASE_MARK(tph, "ref.step");
+  }
+  // F1: orthonormalise X1 (Cholesky QR in FP64)
+  for (int t = tid; t < r * r; t += blockDim.x) {
+    int j = t / r, l = t % r;
+    double acc = 0.0;
+    for (int a = 0; a < m; ++a) acc = fma(sX1[a * r + j], sX1[a * r + l], acc);
+    Gq[t] = acc;
+  }
+  __syncthreads();
+  if (tid == 0) {  // Gq <- L (lower Cholesky factor), in place
+    for (int j = 0; j < r; ++j) {
+      double d = Gq[j * r + j];
+      for (int l = 0; l < j; ++l) d -= Gq[j * r + l] * Gq[j * r + l];
+      d = (d > 0.0) ? sqrt(d) : 0.0;
+      Gq[j * r + j] = d;
+      for (int ii = j + 1; ii < r; ++ii) {
+        double v = Gq[ii * r + j];
+        for (int l = 0; l < j; ++l) v -= Gq[ii * r + l] * Gq[j * r + l];
+        Gq[ii * r + j] = (d > 0.0) ? v / d : 0.0;
+      }
+    }
+  }
+  __syncthreads();
+  // Q = X1 L^-T on own rows: row a solves L y = x (forward substitution)
+  for (int a = lo + tid; a < hi; a += blockDim.x) {
+    double y[RT_MAXR];
+#pragma unroll
+    for (int j = 0; j < RT_MAXR; ++j) {
+      if (j < r) {
+        double v = sX1[a * r + j];
+        for (int l = 0; l < j; ++l) v -= Gq[j * r + l] * y[l];
+        double d = Gq[j * r + j];
+        y[j] = (d > 0.0) ? v / d : 0.0;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < RT_MAXR; ++j)
+      if (j < r) Qw[(long long)a * r + j] = y[j];
+  }
+  cluster_barrier();
+  load_panel(sX1, Qw, m * r);  // sX1 now holds Q
+  __syncthreads();
+  // F2: Yw = M Q on own rows
+  for (int t = tid; t < own * r; t += blockDim.x) {
+    int a = t / r, j = t - a * r;
+    const double* Ma = sM + (size_t)a * m;
+    double acc = 0.0;
+    for (int c = 0; c < m; ++c) acc = fma(Ma[c], sX1[c * r + j], acc);
+    Yw[(long long)(lo + a) * r + j] = acc;
+  }
+  cluster_barrier();
+  load_panel(sYw, Yw, m * r);
+  __syncthreads();
+  PHASE_MARK(tph, "ref.qr+MQ");
+  // F3: H = Q^T M Q (r x r), its eigenpairs by FP64 cyclic Jacobi, cutoff of SVD_r
+  for (int t = tid; t < r * r; t += blockDim.x) {
+    int j = t / r, l = t % r;
+    double acc = 0.0;
+    for (int a = 0; a < m; ++a) acc = fma(sX1[a * r + j], sYw[a * r + l], acc);
+    Hs[t] = acc;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int j = 0; j < r; ++j) {  // symmetrise, identity start
+      for (int l = j + 1; l < r; ++l) {
+        double v = 0.5 * (Hs[j * r + l] + Hs[l * r + j]);
+        Hs[j * r + l] = Hs[l * r + j] = v;
+      }
+      for (int l = 0; l < r; ++l) Yh[j * r + l] = (j == l) ? 1.0 : 0.0;
+    }
+    for (int sw = 0; sw < 50; ++sw) {
+      double off = 0.0, dia = 0.0;
+      for (int j = 0; j < r; ++j)
+        for (int l = 0; l < r; ++l) {
+          if (j != l) off += Hs[j * r + l] * Hs[j * r + l];
+          else dia += Hs[j * r + l] * Hs[j * r + l];
+        }
+      if (off <= 1e-32 * dia) break;
+      for (int p = 0; p < r - 1; ++p)
+        for (int qq = p + 1; qq < r; ++qq) {
+          double apq = Hs[p * r + qq];
+          if (apq == 0.0) continue;
+          double app = Hs[p * r + p], aqq = Hs[qq * r + qq];
+          double theta = (aqq - app) / (2.0 * apq);
+          double tt = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+          double c = 1.0 / sqrt(tt * tt + 1.0), s1 = tt * c;
+          for (int l = 0; l < r; ++l) {  // rows p, q
+            double hp = Hs[p * r + l], hq = Hs[qq * r + l];
+            Hs[p * r + l] = c * hp - s1 * hq;
+            Hs[qq * r + l] = s1 * hp + c * hq;
+          }
+          for (int l = 0; l < r; ++l) {  // columns p, q
+            double hp = Hs[l * r + p], hq = Hs[l * r + qq];
+            Hs[l * r + p] = c * hp - s1 * hq;
+            Hs[l * r + qq] = s1 * hp + c * hq;
+          }
+          Hs[p * r + qq] = Hs[qq * r + p] = 0.0;
+          for (int l = 0; l < r; ++l) {
+            double yp = Yh[l * r + p], yq = Yh[l * r + qq];
+            Yh[l * r + p] = c * yp - s1 * yq;
+            Yh[l * r + qq] = s1 * yp + c * yq;
+          }
+        }
+    }
+    for (int j = 0; j < r; ++j) order[j] = j;
+    for (int j = 0; j < r; ++j)  // sort eigenvalues descending (selection)
+      for (int l = j + 1; l < r; ++l)
+        if (Hs[order[l] * r + order[l]] > Hs[order[j] * r + order[j]]) {
+          int t = order[j]; order[j] = order[l]; order[l] = t;
+        }
+    double s1 = sqrt(fmax(Hs[order[0] * r + order[0]], 0.0));
+    double tau = (double)max(m, q) * 5.9604644775390625e-08 * s1;  // max(m,q) * 2^-24 * s_1
+    int kept = 0;
+    for (int j = 0; j < r; ++j) {
+      double sj = sqrt(fmax(Hs[order[j] * r + order[j]], 0.0));
+      bool keep = (sj > tau) && (s1 > 0.0);
+      wv[j] = keep ? sj : 0.0;
+      kept += keep ? 1 : 0;
+    }
+    int fl = 0;
+    if (kept < r) fl |= 1;   // RTCUR_FLAG_RANK_DEFICIENT
+    if (tie) fl |= 2;        // RTCUR_FLAG_TIE
+    if (crank != 0) fl &= 2;
+    if (fl) atomicOr(&b.st->flags, fl);
+  }
+  __syncthreads();
+  // Q_r = Q Yh(:, order) on own rows, singular values
+  for (int t = tid; t < own * r; t += blockDim.x) {
+    int a = lo + t / r, j = t % r;
+    double acc = 0.0;
+    for (int l = 0; l < r; ++l) acc = fma(sX1[a * r + l], Yh[l * r + order[j]], acc);
+    Qr[(long long)a * r + j] = (wv[j] > 0.0) ? acc : 0.0;
+  }
+  if (crank == 0 && tid < r) sig[tid] = wv[tid];
+  PHASE_MARK(tph, "ref.rr");
+  cluster_barrier();
+  load_panel(sE, Qr, m * r);  // sE now holds Q_r
+  __syncthreads();
+  // F4: Y = W^T Q_r Sigma^-2 (q x r) on own columns of W, staged kWChunk columns at a time
+  const int blo = (q * crank) / RT_CLUSTER, bhi = (q * (crank + 1)) / RT_CLUSTER;
+  for (int c0 = blo; c0 < bhi; c0 += kWChunk) {
+    const int cn = min(kWChunk, bhi - c0);
+    for (int t = tid; t < m * cn; t += blockDim.x) {
+      int cc = t / m, a = t - cc * m;
+      sW[a * kWChunk + cc] = w_entry(g, b, set, i, a, c0 + cc);
+    }
+    __syncthreads();
+    for (int t = tid; t < cn * r; t += blockDim.x) {
+      int cc = t / r, j = t - cc * r;
+      double acc = 0.0;
+      if (wv[j] > 0.0) {
+        for (int a = 0; a < m; ++a) acc = fma((double)sW[a * kWChunk + cc], sE[a * r + j], acc);
+        acc /= wv[j] * wv[j];
+      }
+      Yout[(long long)(c0 + cc) * r + j] = acc;
+    }
+    __syncthreads();
+  }
+  PHASE_MARK(tph, "ref.Y");
+}
+
+}  // namespace
+
+size_t jacobi_smem_bytes(int m) {
+  int N = m + (m & 1);
+  int P = N / 2;
+  return sizeof(float) * ((size_t)(N * (N + 1)) / 2 + (size_t)m * (N + 1)) +
+         (size_t)P * (2 * sizeof(int) + 3 * sizeof(float));
+}
+
+cudaError_t launch_gram(const Geom& g, const Bufs& b, cudaStream_t s) {
+  int blocks = 0;
+  for (int i = 0; i < g.n; ++i) {
+    int nt = (g.m[i] + kGramTile - 1) / kGramTile;
+    blocks += nt * (nt + 1) / 2;
+  }
+  k_gram<<<blocks, kGramTile * kGramTile, 0, s>>>(g, b);
+  return cudaGetLastError();
+}
+
+constexpr size_t kFullSmem = sizeof(float) * 3 * kFullMaxN * kFullLd;
+constexpr size_t kTriSmem = sizeof(float) * 3 * kTriMax * kTriLd;
+
+cudaError_t prepare_jacobi(size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_eig_tri, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTriSmem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_jacobi_full, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFullSmem);
+}
+
+cudaError_t launch_jacobi(const Geom& g, const Bufs& b, cudaStream_t s) {
+  int mx = 0;
+  for (int i = 0; i < g.n; ++i) mx = g.m[i] > mx ? g.m[i] : mx;
+  if (mx <= kTriMax && g.eig_method == 0) {
+    k_eig_tri<<<g.n, kJacThreads, kTriSmem, s>>>(g, b);
+    return cudaGetLastError();
+  }
+  if (mx <= kFullMaxN) {
+    k_jacobi_full<<<g.n, kJacThreads, kFullSmem, s>>>(g, b, g.warm_start);
+    return cudaGetLastError();
+  }
+  size_t sm = jacobi_smem_bytes(mx);
+  k_jacobi<<<g.n, kJacThreads, sm, s>>>(g, b);
+  return cudaGetLastError();
+}
+
+size_t refine_smem_max(const Geom& g) {
+  size_t mx = 0;
+  for (int i = 0; i < g.n; ++i) {
+    size_t v = refine_smem_bytes(g.m[i], g.r[i]);
+    mx = v > mx ? v : mx;
+  }
+  return mx;
+}
+
+cudaError_t prepare_refine(const Geom& g) {
+  return cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)refine_smem_max(g));
+}
+
+cudaError_t launch_refine(const Geom& g, const Bufs& b, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(RT_CLUSTER * g.n);
+  cfg.blockDim = dim3(kRefThreads);
+  cfg.dynamicSmemBytes = refine_smem_max(g);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = RT_CLUSTER;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_refine, g, b);
+}

@@ -1,0 +1,324 @@
+// Sampled-entry kernels of one RTCUR iteration.
+//
+//  sample_ht   Step (I) on the sample: S^(k+1) = HT_{zeta^(k+1)}(X - L^(k)) on R's entries and on
+//              the fibers of C_i (Eq. partial S update), writing (X - S) into the sample buffer,
+//              which then holds R^(k+1) and C_i^(k+1) of Eq. (R, C_i, U_i).
+//  sample_err  e^(k+1) of Eq. (rel_err): per-segment Frobenius norms of E = X - L^(k+1) - S^(k+1)
+//              over this iteration's sets, divided by those of X.
+//  commit      k <- k+1, zeta <- gamma zeta (Sec. 3.2 decay), histories, loop condition.
+//
+// Reductions are deterministic: per-block partials in a fixed slot, then the last block to
+// finish sums them in block order.
+#include "rtcur_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxRedBlocks = 1024;
+
+__device__ __forceinline__ const long long* current_set(const Geom& g, const Bufs& b, int k) {
+  long long s = (g.variant == 1) ? (long long)(k % g.n_sets) : 0;
+  return b.idx + s * g.set_len;
+}
+
+// Block-wide sum of `v` (kThreads threads); result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < kThreads / 32; ++i) t += sh[i];
+  return t;
+}
+
+// Sum of slot `slot` over the first `nb` block partials, by the whole block (fixed order per
+// thread, then a block sum); result valid in thread 0.
+__device__ __forceinline__ double sum_partials(const double* part, int nb, int slot, double* sh) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += part[i * RT_RED_SLOTS + slot];
+  return block_sum(acc, sh);
+}
+
+__global__ void k_setup(Geom g, Bufs b, double zeta0) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  State* st = b.st;
+  st->k = 0;
+  st->err = 0;
+  st->flags = 0;
+  st->zeta = zeta0;
+  st->zeta0 = zeta0;
+  st->e = 1.0;  // L^(0) = S^(0) = 0 gives E = X
+  st->e_stage = 1.0;
+  st->cont = (g.max_iter > 0 && 1.0 > g.tol) ? 1 : 0;
+  st->nnz_s = st->inband_s = 0;
+  st->jsweeps = 0;
+  st->nnz_f = st->inband_f = -1;
+  st->resid_f = -1.0;
+  for (int i = 0; i < RT_MAXN + 1; ++i) st->den[i] = st->num[i] = 0.0;
+  for (int i = 0; i < TK_COUNT; ++i) b.ticket[i] = 0u;
+}
+
+__global__ void __launch_bounds__(kThreads) k_maxabs(Geom g, Bufs b) {
+  __shared__ double sh[kThreads / 32];
+  const float* X = b.sp->X;
+  float mx = 0.f;
+  long long stride = (long long)gridDim.x * kThreads;
+  for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < g.N; i += stride)
+    mx = fmaxf(mx, fabsf(__ldg(X + i)));
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  double* part = b.red + (size_t)TK_MAXABS * kMaxRedBlocks * RT_RED_SLOTS;
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int i = 0; i < kThreads / 32; ++i) m = fmax(m, sh[i]);
+    part[blockIdx.x] = m;
+  }
+  if (last_block_arrive(b.ticket + TK_MAXABS)) {
+    double m = 0.0;
+    for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) m = fmax(m, part[i]);
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int i = 0; i < kThreads / 32; ++i) m = fmax(m, sh[i]);
+      b.st->zeta = m;
+      b.st->zeta0 = m;
+      b.ticket[TK_MAXABS] = 0u;
+    }
+  }
+}
+
+// Xs[e] = X at sampled entry e and rc[e] = (row of T, column of B_n) for the fixed sets
+// (gathered once per solve).
+__global__ void __launch_bounds__(kThreads) k_gather_x(Geom g, Bufs b) {
+  const long long* set = current_set(g, b, 0);
+  const float* X = b.sp->X;
+  long long p[RT_MAXN];
+  long long stride = (long long)gridDim.x * kThreads;
+  for (long long e = (long long)blockIdx.x * kThreads + threadIdx.x; e < g.nS; e += stride) {
+    sample_coords(g, set, e, p);
+    long long row = table_row(g, p), col = p[g.n - 1];
+    b.rc[e] = make_uint2((unsigned)row, (unsigned)col);
+    b.Xs[e] = __ldg(X + row * g.d[g.n - 1] + col);
+  }
+}
+
+// Segment of entry e (0 = R, 1 + i = C_i).
+__device__ __forceinline__ int segment_of(const Geom& g, long long e) {
+  int s = 0;
+  while (s < g.n && e >= g.seg[s + 1]) ++s;
+  return s;
+}
+
+__global__ void __launch_bounds__(kThreads) k_sample_ht(Geom g, Bufs b) {
+  __shared__ double sh[kThreads / 32];
+  const State* st = b.st;
+  const int k = st->k;
+  const int cur = k & 1;
+  const double zeta = g.gamma * st->zeta;  // zeta^(k+1)
+  const float zf = (float)zeta;
+  const float band = (float)(g.inband * zeta);
+  const long long* set = current_set(g, b, k);
+  const int* pos = b.pos + ((g.variant == 1) ? (long long)(k % g.n_sets) : 0LL) * g.sumD;
+  const float* X = b.sp->X;
+  const float* T = b.T[cur];
+  const float* Bn = b.B[cur] + g.offB[g.n - 1];
+  const int rn = g.rlast;
+  const long long dn = g.d[g.n - 1];
+  float den[RT_MAXN + 1];
+#pragma unroll
+  for (int s = 0; s < RT_MAXN + 1; ++s) den[s] = 0.f;
+  float nnz = 0.f, inb = 0.f, bad = 0.f;
+  long long p[RT_MAXN];
+  long long stride = (long long)gridDim.x * kThreads;
+  for (long long e = (long long)blockIdx.x * kThreads + threadIdx.x; e < g.nS; e += stride) {
+    long long row, col;
+    float x;
+    int seg;
+    if (g.variant == 1) {
+      seg = sample_coords(g, set, e, p);
+      row = table_row(g, p);
+      col = p[g.n - 1];
+      b.rc[e] = make_uint2((unsigned)row, (unsigned)col);
+      x = __ldg(X + row * dn + col);
+    } else {
+      uint2 rc = b.rc[e];
+      row = rc.x;
+      col = rc.y;
+      x = b.Xs[e];
+      seg = segment_of(g, e);
+    }
+    float L = eval_L(T, Bn, rn, row, col);
+    float dlt = x - L;
+    float ad = fabsf(dlt);
+    bool keep = ad > zf;                 // HT_zeta keeps |x| > zeta (strict)
+    const float xs = keep ? L : x;       // (X - S) = X - (X - L) = L where S is nonzero
+    b.XS[e] = xs;
+    if (seg > 0) {                       // fiber entry: also W_i = C_i(I_i, :) when t is in I_i
+      const int i = seg - 1;
+      const unsigned local = (unsigned)(e - g.seg[seg]);
+      const unsigned bcol = local / (unsigned)g.d[i];
+      const unsigned t = local - bcol * (unsigned)g.d[i];
+      const int a = pos[g.offD[i] + t];
+      if (a >= 0) b.W[g.offW[i] + (long long)a * g.q[i] + bcol] = xs;
+    }
+    nnz += keep ? 1.f : 0.f;
+    inb += (fabsf(ad - zf) <= band) ? 1.f : 0.f;
+    if (!isfinite(x)) bad += 1.f;
+    float xx = x * x;
+#pragma unroll
+    for (int s = 0; s < RT_MAXN + 1; ++s)
+      if (s == seg) den[s] += xx;
+  }
+  double* part = b.red + (size_t)TK_SAMPLE * kMaxRedBlocks * RT_RED_SLOTS;
+  double tot;
+#pragma unroll
+  for (int s = 0; s < RT_MAXN + 1; ++s) {
+    tot = block_sum((double)den[s], sh);
+    if (threadIdx.x == 0) part[blockIdx.x * RT_RED_SLOTS + s] = tot;
+  }
+  tot = block_sum((double)nnz, sh);
+  if (threadIdx.x == 0) part[blockIdx.x * RT_RED_SLOTS + 5] = tot;
+  tot = block_sum((double)inb, sh);
+  if (threadIdx.x == 0) part[blockIdx.x * RT_RED_SLOTS + 6] = tot;
+  tot = block_sum((double)bad, sh);
+  if (threadIdx.x == 0) part[blockIdx.x * RT_RED_SLOTS + 7] = tot;
+  if (last_block_arrive(b.ticket + TK_SAMPLE)) {
+    State* w = b.st;
+    for (int slot = 0; slot < 8; ++slot) {
+      double acc = sum_partials(part, gridDim.x, slot, sh);
+      if (threadIdx.x == 0) {
+        if (slot < RT_MAXN + 1) w->den[slot] = acc;
+        if (slot == 5) w->nnz_s = (long long)acc;
+        if (slot == 6) w->inband_s = (long long)acc;
+        if (slot == 7 && acc > 0.0) w->err = -4;  // RTCUR_ENONFINITE
+      }
+    }
+    if (threadIdx.x == 0) {
+      w->jsweeps = 0;
+      b.ticket[TK_SAMPLE] = 0u;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_sample_err(Geom g, Bufs b) {
+  __shared__ double sh[kThreads / 32];
+  const State* st = b.st;
+  const int k = st->k;
+  const int nxt = (k + 1) & 1;
+  const float* T = b.T[nxt];
+  const float* Bn = b.B[nxt] + g.offB[g.n - 1];
+  const int rn = g.rlast;
+  float num[RT_MAXN + 1];
+#pragma unroll
+  for (int s = 0; s < RT_MAXN + 1; ++s) num[s] = 0.f;
+  long long stride = (long long)gridDim.x * kThreads;
+  for (long long e = (long long)blockIdx.x * kThreads + threadIdx.x; e < g.nS; e += stride) {
+    uint2 rc = b.rc[e];
+    int seg = segment_of(g, e);
+    float L = eval_L(T, Bn, rn, rc.x, rc.y);
+    float E = b.XS[e] - L;   // X - S^(k+1) - L^(k+1)
+    float ee = E * E;
+#pragma unroll
+    for (int s = 0; s < RT_MAXN + 1; ++s)
+      if (s == seg) num[s] += ee;
+  }
+  double* part = b.red + (size_t)TK_ERR * kMaxRedBlocks * RT_RED_SLOTS;
+#pragma unroll
+  for (int s = 0; s < RT_MAXN + 1; ++s) {
+    double tot = block_sum((double)num[s], sh);
+    if (threadIdx.x == 0) part[blockIdx.x * RT_RED_SLOTS + s] = tot;
+  }
+  if (last_block_arrive(b.ticket + TK_ERR)) {
+    State* w = b.st;
+    double sn = 0.0, sd = 0.0;
+    for (int s = 0; s <= g.n; ++s) {
+      double acc = sum_partials(part, gridDim.x, s, sh);
+      if (threadIdx.x == 0) {
+        w->num[s] = acc;
+        sn += sqrt(acc);
+        sd += sqrt(w->den[s]);
+      }
+    }
+    if (threadIdx.x == 0) {
+      w->e_stage = (sd > 0.0) ? sn / sd : 0.0;
+      b.ticket[TK_ERR] = 0u;
+    }
+  }
+}
+
+__global__ void k_commit(Geom g, Bufs b, unsigned long long handle, int use_handle) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  State* st = b.st;
+  int k = st->k;
+  double zeta = g.gamma * st->zeta;
+  double e = st->e_stage;
+  if (k < g.max_iter) {
+    b.e_hist[k] = e;
+    b.z_hist[k] = zeta;
+    b.nnz_hist[k] = st->nnz_s;
+  }
+  st->zeta = zeta;
+  st->e = e;
+  st->k = k + 1;
+  int cont = (e > g.tol) && (k + 1 < g.max_iter) && (st->err == 0);
+  st->cont = cont;
+  if (use_handle) cudaGraphSetConditional((cudaGraphConditionalHandle)handle, cont ? 1u : 0u);
+}
+
+__global__ void k_gate(Bufs b, unsigned long long handle) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  cudaGraphSetConditional((cudaGraphConditionalHandle)handle, b.st->cont ? 1u : 0u);
+}
+
+int grid_for(long long work) {
+  long long g = (work + kThreads - 1) / kThreads;
+  if (g < 1) g = 1;
+  if (g > kMaxRedBlocks) g = kMaxRedBlocks;
+  return (int)g;
+}
+
+}  // namespace
+
+cudaError_t launch_setup(const Geom& g, const Bufs& b, double zeta0, int use_maxabs, cudaStream_t s) {
+  k_setup<<<1, 32, 0, s>>>(g, b, zeta0);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !use_maxabs) return e;
+  return launch_maxabs(g, b, s);
+}
+
+cudaError_t launch_maxabs(const Geom& g, const Bufs& b, cudaStream_t s) {
+  k_maxabs<<<grid_for(g.N), kThreads, 0, s>>>(g, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_x(const Geom& g, const Bufs& b, cudaStream_t s) {
+  k_gather_x<<<grid_for(g.nS), kThreads, 0, s>>>(g, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sample_ht(const Geom& g, const Bufs& b, cudaStream_t s) {
+  k_sample_ht<<<grid_for(g.nS), kThreads, 0, s>>>(g, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sample_err(const Geom& g, const Bufs& b, cudaStream_t s) {
+  k_sample_err<<<grid_for(g.nS), kThreads, 0, s>>>(g, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_commit(const Geom& g, const Bufs& b, unsigned long long handle, int use_handle,
+                          cudaStream_t s) {
+  k_commit<<<1, 32, 0, s>>>(g, b, handle, use_handle);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gate(const Bufs& b, unsigned long long handle, cudaStream_t s) {
+  k_gate<<<1, 32, 0, s>>>(b, handle);
+  return cudaGetLastError();
+}

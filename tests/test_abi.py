@@ -1,0 +1,64 @@
+"""The C-ABI library builds, loads and exports every entry point include/rtcur.h declares, and
+rejects invalid arguments before touching a GPU (CPU only)."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2108_10448_gb300 import rtcur as rt
+    return rt.load()
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "rtcur.h")).read()
+    return sorted(set(re.findall(r"RTCUR_API\s+[\w\s\*]+?\b(rtcur_\w+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 9
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+@pytest.mark.parametrize("kw,msg", [
+    (dict(dims=[10, 10, 10, 10, 10]), "n_modes"),
+    (dict(gamma=1.0), "gamma"),
+    (dict(gamma=0.0), "gamma"),
+    (dict(tol=float("nan")), "tol"),
+    (dict(max_iter=0), "max_iter"),
+    (dict(variant=2), "variant"),
+    (dict(ranks=[0, 2, 2]), "ranks"),
+    (dict(nI=[1, 4, 4]), "nI"),
+    (dict(nI=[11, 4, 4]), "nI"),
+    (dict(nJ=[101, 8, 8]), "nJ"),
+])
+def test_create_rejects_invalid_arguments(lib, kw, msg):
+    from paper_2108_10448_gb300 import rtcur as rt
+    args = dict(dims=[10, 10, 10], ranks=[2, 2, 2], nI=[4, 4, 4], nJ=[8, 8, 8], zeta0=1.0,
+                gamma=0.7, tol=1e-5, max_iter=10, variant=0)
+    args.update(kw)
+    n = len(args["dims"])
+    for key in ("ranks", "nI", "nJ"):
+        if len(args[key]) < n:
+            args[key] = list(args[key]) + [args[key][-1]] * (n - len(args[key]))
+    with pytest.raises(rt.RTCURError) as ei:
+        rt.rtcur_create(**args)
+    assert ei.value.status == rt.EINVAL
+    assert msg in str(ei.value)
+
+
+def test_options_reserved_must_be_zero(lib):
+    from paper_2108_10448_gb300 import rtcur as rt
+    o = rt.make_options()
+    o.reserved[3] = 1
+    with pytest.raises(rt.RTCURError) as ei:
+        rt.rtcur_create([8, 8, 8], [2, 2, 2], [4, 4, 4], [8, 8, 8], 1.0, 0.7, 1e-5, 5, 0, o)
+    assert ei.value.status == rt.EINVAL
