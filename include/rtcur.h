@@ -147,6 +147,29 @@ RTCUR_API rtcur_status rtcur_finish(rtcur_plan* plan, float* L_out, float* S_out
  * rtcur_finish reports. Does not advance k. No host sync. */
 RTCUR_API rtcur_status rtcur_threshold_dense(rtcur_plan* plan, int32_t n_launch, void* stream);
 
+/* rtcur_threshold_dense_noalloc -- the dense fused threshold pass, S = HT_zeta(X - L) with
+ * L = G x_1 B_1 ... x_n B_n, for callers that cannot allocate device memory. The paper has no
+ * counterpart: it is an allocation-free form of rtcur_threshold_dense for callers such as a
+ * serving process whose device memory belongs to a pre-reserved pool with a hard budget, or a
+ * latency-critical caller that cannot afford cudaMalloc's possible implicit synchronisation.
+ *   n_modes, dims, ranks   geometry as in rtcur_create
+ *   G      device, prod r_i floats (row-major core);  B  device, sum d_i r_i floats (B_i is d_i x r_i
+ *          row-major, packed mode after mode) -- the layout rtcur_get_factors returns
+ *   X      device, prod d_i floats, 16-byte aligned;  S  device output, prod d_i floats, 16-byte aligned
+ *   zeta   threshold used as given (HT keeps |x - L| > zeta, compared in FP32)
+ *   counts host double[3] or NULL: {||X - L - S||_F^2, nnz(S), band count}; when given, the call
+ *          synchronises `stream`
+ * Scratch: one fixed 32 MiB device array inside the library (held by every GPU that loads it
+ * until the process exits); problems needing more (prod_{i<n} d_i * r_n + 4 floats of table plus
+ * ~1.1 MB) return RTCUR_EINVAL. Nothing is allocated: no cudaMalloc, no cudaFree. The first call
+ * on each device (with that device current) looks up the array's device address and caches it;
+ * make that first call before any stream capture. All calls share the array, so calls that
+ * overlap on the GPU race; the parts that must start at zero are cleared at every call. */
+RTCUR_API rtcur_status rtcur_threshold_dense_noalloc(int32_t n_modes, const int64_t* dims,
+                                                     const int32_t* ranks, const float* G,
+                                                     const float* B, const float* X, double zeta,
+                                                     float* S, double* counts, void* stream);
+
 /* rtcur_get_factors -- copy the current L^(k) in Tucker form L = G x_1 B_1 ... x_n B_n to host
  * arrays (FP32): G has prod r_i entries (row-major), B_i is d_i x r_i row-major, packed mode
  * after mode in B (sum d_i r_i entries). This is the same tensor as R x_i (C_i U_i^+) of

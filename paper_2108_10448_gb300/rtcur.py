@@ -60,6 +60,9 @@ def load(path=LIB_PATH):
     lib.rtcur_iterate.argtypes = [P, C.c_int32, P]
     lib.rtcur_finish.argtypes = [P, P, P, C.POINTER(rtcur_result), P]
     lib.rtcur_threshold_dense.argtypes = [P, C.c_int32, P]
+    lib.rtcur_threshold_dense_noalloc.argtypes = [C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                                  P, P, P, C.c_double, P, C.POINTER(C.c_double), P]
+    lib.rtcur_threshold_dense_noalloc.restype = C.c_int
     lib.rtcur_get_factors.argtypes = [P, C.POINTER(C.c_float), C.POINTER(C.c_float),
                                       C.POINTER(C.c_int32), C.POINTER(C.c_double), P]
     lib.rtcur_sample_count.argtypes = [P]
@@ -180,6 +183,20 @@ def rtcur_finish(plan, L_ptr=0, S_ptr=0, stream=0, max_iter=1000):
 
 def rtcur_threshold_dense(plan, n_launch=1, stream=0):
     _check(load().rtcur_threshold_dense(plan, int(n_launch), stream or None), plan)
+
+
+def rtcur_threshold_dense_noalloc(dims, ranks, G_ptr, B_ptr, X_ptr, zeta, S_ptr, stream=0,
+                                  want_counts=True):
+    """Allocation-free dense threshold pass S = HT_zeta(X - G x_i B_i) (device pointers). For
+    callers that cannot allocate device memory; its scratch is a fixed array inside the library.
+    Returns (resid, nnz, band) when want_counts, else None."""
+    counts = (C.c_double * 3)()
+    st = load().rtcur_threshold_dense_noalloc(len(dims), _i64(dims), _i32(ranks), G_ptr, B_ptr, X_ptr,
+                                              float(zeta), S_ptr, counts if want_counts else None,
+                                              stream or None)
+    if st != OK:
+        raise RTCURError(st, "rtcur_threshold_dense_noalloc failed")
+    return (counts[0], int(counts[1]), int(counts[2])) if want_counts else None
 
 
 def rtcur_get_factors(plan, dims, ranks, stream=0):
