@@ -288,6 +288,7 @@ def run_ours(a, rank, world):
                    "l2": "inputs larger than L2 (X is 2.05 GB), no flush",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "time_to_tol": {"ms": ttt_ms, "iters": res.iters, "e": res.e, "status": res.status,
+                        "warm_hits": res.warm_hits,
                         "includes": "index upload, max|X|, the graph-driven loop, L and S output"},
         "e2e": {"value": e2e_val, "unit": "iters/s", "seconds": e2e_s, "iters": res_e2e.iters,
                 "h2d_bytes_per_step": int(p.X.nbytes), "d2h_bytes_per_step": int(p.X.nbytes),

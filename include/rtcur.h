@@ -92,6 +92,8 @@ typedef struct rtcur_result {
   int64_t nnz_full;     /* FULL scope: nonzeros of S^(k) over the whole tensor; else -1 */
   int64_t inband_full;  /* FULL scope: the band count over the whole tensor; else -1 */
   double resid_full;    /* FULL scope: ||X - L^(k-1) - S^(k)||_F^2 over the whole tensor; else -1 */
+  int64_t warm_hits;    /* (iteration, mode) pairs whose truncated SVD came from the certified
+                           warm-started subspace iteration instead of the full eigensolver */
   /* Optional per-iteration histories: caller arrays of max_iter entries, or NULL. */
   double* e_hist;
   double* zeta_hist;

@@ -11,6 +11,7 @@
 // whole solve runs on the device with one host synchronisation at the end.
 #include <cmath>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -83,8 +84,9 @@ cudaError_t capture_body(rtcur_plan* p, cudaStream_t s, unsigned long long handl
   }
   if ((e = launch_sample_ht(g, b, s)) != cudaSuccess) return e;
   if ((e = launch_gram(g, b, s)) != cudaSuccess) return e;
+  if ((e = launch_refine(g, b, 0, s)) != cudaSuccess) return e;  // warm attempt
   if ((e = launch_jacobi(g, b, s)) != cudaSuccess) return e;
-  if ((e = launch_refine(g, b, s)) != cudaSuccess) return e;
+  if ((e = launch_refine(g, b, 1, s)) != cudaSuccess) return e;
   if ((e = launch_factor_B(g, b, s)) != cudaSuccess) return e;
   if ((e = launch_core(g, b, s)) != cudaSuccess) return e;
   if ((e = launch_table(g, b, 1, s)) != cudaSuccess) return e;
@@ -216,6 +218,7 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
   g.max_sweeps = o.jacobi_max_sweeps;
   g.warm_start = 0;
   g.eig_method = o.eig_method;
+  { const char* ev = getenv("RTCUR_DENSE_CTAS"); g.dense_ctas = ev ? atoi(ev) : 0; }
   g.gamma = gamma;
   g.tol = tol;
   g.inband = o.inband_rel;
@@ -309,7 +312,8 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
   AL(b.Qr, oQ);
   AL(b.sig, oR);
   AL(b.Y, oY);
-  AL(b.ework, 3 * oQ);
+  AL(b.ework, 3 * oQ + 2 * 16 * RT_MAXN);
+  AL(b.warm, RT_MAXN);
   AL(b.Bpart, g.nchunk * g.sumB);
   AL(b.B[0], g.sumB);
   AL(b.B[1], g.sumB);
@@ -327,8 +331,12 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
   AL(b.nnz_hist, max_iter);
   if (o.scope == RTCUR_SCOPE_FULL) AL(p->S_internal, g.N);
 #undef AL
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking);
+  // the latency-bound sampled chain is captured from a high-priority stream, the bandwidth-bound
+  // dense pass from a low-priority one (kernel nodes keep their stream's priority)
+  int prio_lo = 0, prio_hi = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&p->cap, cudaStreamNonBlocking, prio_hi);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&p->side, cudaStreamNonBlocking, prio_lo);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->evFork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->evJoin, cudaEventDisableTiming);
   if (e == cudaSuccess) {
@@ -336,7 +344,7 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
     e = prepare_jacobi(sm);
   }
   if (e == cudaSuccess) e = prepare_dense(g);
-  if (e == cudaSuccess) e = prepare_refine(g);
+  if (e == cudaSuccess) e = prepare_refine(p->g);
   if (e == cudaSuccess) e = cudaMemset(b.ticket, 0, sizeof(unsigned) * TK_COUNT);
   if (e != cudaSuccess) {
     rtcur_status st = (e == cudaErrorMemoryAllocation) ? RTCUR_ENOMEM : RTCUR_ECUDA;
@@ -378,6 +386,7 @@ rtcur_status rtcur_begin(rtcur_plan* p, const float* X, const int64_t* idx, floa
   CKC(p, cudaMemsetAsync(b.T[0], 0, sizeof(float) * g.rowsT * g.rlast, s));
   CKC(p, cudaMemsetAsync(b.B[0], 0, sizeof(float) * g.sumB, s));
   CKC(p, cudaMemsetAsync(b.G[0], 0, sizeof(float) * g.nG, s));
+  CKC(p, cudaMemsetAsync(b.warm, 0, sizeof(int) * RT_MAXN, s));
   CKC(p, launch_setup(g, b, p->zeta0, p->zeta0 <= 0.0 ? 1 : 0, s));
   if (g.variant == RTCUR_VARIANT_F) CKC(p, launch_gather_x(g, b, s));
   p->X = X;
@@ -419,6 +428,7 @@ rtcur_status rtcur_finish(rtcur_plan* p, float* L_out, float* S_out, rtcur_resul
     res->iters = h.k;
     res->flags = h.flags;
     res->jacobi_sweeps = h.jsweeps;
+    res->warm_hits = h.warm_hits;
     res->e = h.e;
     res->zeta = h.zeta;
     res->nnz_sample = h.nnz_s;

@@ -190,19 +190,25 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
       : "memory");
 }
 
-template <int RN>
-__global__ void __launch_bounds__(1024, 1) k_dense_tma(Geom g, Bufs b, int tr) {
+// MODE 0: the fused threshold pass of an iteration (L^(k), zeta^(k+1), S into the solve's S
+//         buffer, reductions). MODE 1: write L of copy `copy_sel` (0 = current, 1 = previous)
+//         into `out` (no X read). MODE 2: write HT_{zeta^(k)}(X - L) of copy `copy_sel` into
+//         `out` (zero when k = 0). Modes 1 and 2 materialise the solve's outputs.
+template <int RN, int MODE>
+__global__ void __launch_bounds__(1024, 1) k_dense_tma(Geom g, Bufs b, int tr, int copy_sel, float* out) {
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ unsigned long long full[kStages];
   __shared__ double sh[32];
   __shared__ int abort_flag;
   const State* st = b.st;
-  const int cur = st->k & 1;
-  const double zeta = g.gamma * st->zeta;
+  const int kk = st->k;
+  const int cur = (MODE == 0) ? (kk & 1) : ((kk + copy_sel) & 1);
+  const double zeta = (MODE == 0) ? g.gamma * st->zeta : st->zeta;
   const float zf = (float)zeta;
   const float band = (float)(g.inband * zeta);
+  const bool zero_out = (MODE == 2) && (kk == 0);
   const float* __restrict__ X = b.sp->X;
-  float* __restrict__ S = b.sp->S;
+  float* __restrict__ S = (MODE == 0) ? b.sp->S : out;
   const float* __restrict__ T = b.T[cur];
   const float* __restrict__ Bn = b.B[cur] + g.offB[g.n - 1];
   const long long dn = g.d[g.n - 1];
@@ -242,11 +248,11 @@ __global__ void __launch_bounds__(1024, 1) k_dense_tma(Geom g, Bufs b, int tr) {
       if (t < ntiles) {
         long long r0 = t * tr;
         long long nr = (r0 + tr <= rows ? tr : rows - r0);
-        unsigned bytes = (unsigned)(nr * dn * 4);
+        unsigned bytes = (MODE == 1) ? 0u : (unsigned)(nr * dn * 4);
         long long a0 = (r0 * RN) & ~3LL, a1 = ((r0 + nr) * RN + 3) & ~3LL;
         unsigned tbytes = (unsigned)((a1 - a0) * 4);
         mbar_expect_tx(&full[s], bytes + tbytes);
-        bulk_g2s(ring + (size_t)s * stage_f4, X + r0 * dn, bytes, &full[s]);
+        if (bytes) bulk_g2s(ring + (size_t)s * stage_f4, X + r0 * dn, bytes, &full[s]);
         bulk_g2s(tring + (size_t)s * tstage, T + a0, tbytes, &full[s]);
         issued[s] = 1;
       }
@@ -284,12 +290,17 @@ __global__ void __launch_bounds__(1024, 1) k_dense_tma(Geom g, Bufs b, int tr) {
           L2 = fmaf(tv[c], br[2][c], L2);
           L3 = fmaf(tv[c], br[3][c], L3);
         }
-        float4 xv = tile[rr * n4 + c4];
         float4 sv;
-        ht_acc(xv.x, L0, zf, band, sv.x, res, nnz, inb);
-        ht_acc(xv.y, L1, zf, band, sv.y, res, nnz, inb);
-        ht_acc(xv.z, L2, zf, band, sv.z, res, nnz, inb);
-        ht_acc(xv.w, L3, zf, band, sv.w, res, nnz, inb);
+        if (MODE == 1) {
+          sv = make_float4(L0, L1, L2, L3);
+        } else {
+          float4 xv = tile[rr * n4 + c4];
+          ht_acc(xv.x, L0, zf, band, sv.x, res, nnz, inb);
+          ht_acc(xv.y, L1, zf, band, sv.y, res, nnz, inb);
+          ht_acc(xv.z, L2, zf, band, sv.z, res, nnz, inb);
+          ht_acc(xv.w, L3, zf, band, sv.w, res, nnz, inb);
+          if (zero_out) sv = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         __stcs(reinterpret_cast<float4*>(S + r * dn) + c4, sv);
       }
     }
@@ -299,11 +310,11 @@ __global__ void __launch_bounds__(1024, 1) k_dense_tma(Geom g, Bufs b, int tr) {
       if (tn < ntiles) {
         long long rn0 = tn * tr;
         long long nr2 = (rn0 + tr <= rows ? tr : rows - rn0);
-        unsigned bytes = (unsigned)(nr2 * dn * 4);
+        unsigned bytes = (MODE == 1) ? 0u : (unsigned)(nr2 * dn * 4);
         long long a0 = (rn0 * RN) & ~3LL, a1 = ((rn0 + nr2) * RN + 3) & ~3LL;
         unsigned tbytes = (unsigned)((a1 - a0) * 4);
         mbar_expect_tx(&full[s], bytes + tbytes);
-        bulk_g2s(ring + (size_t)s * stage_f4, X + rn0 * dn, bytes, &full[s]);
+        if (bytes) bulk_g2s(ring + (size_t)s * stage_f4, X + rn0 * dn, bytes, &full[s]);
         bulk_g2s(tring + (size_t)s * tstage, T + a0, tbytes, &full[s]);
 #pragma unroll
         for (int s2 = 0; s2 < kStages; ++s2) issued[s2] += (s2 == s) ? 1 : 0;
@@ -323,6 +334,7 @@ __global__ void __launch_bounds__(1024, 1) k_dense_tma(Geom g, Bufs b, int tr) {
     __syncthreads();
   }
   (void)tile_bytes_full;
+  if (MODE != 0) return;
   double* part = b.red + (size_t)TK_DENSE * kMaxRedBlocks * RT_RED_SLOTS;
   const int bid = blockIdx.x;
   double t0 = block_sum_d((double)res, sh);
@@ -349,14 +361,31 @@ __global__ void __launch_bounds__(1024, 1) k_dense_tma(Geom g, Bufs b, int tr) {
 
 template <int RN>
 cudaError_t launch_tma_rn(const Geom& g, const Bufs& b, int tr, size_t smem, int grid, int threads,
-                          cudaStream_t s) {
-  k_dense_tma<RN><<<grid, threads, smem, s>>>(g, b, tr);
+                          cudaStream_t s, int mode = 0, int copy_sel = 0, float* out = nullptr) {
+  if (mode == 0)
+    k_dense_tma<RN, 0><<<grid, threads, smem, s>>>(g, b, tr, copy_sel, out);
+  else if (mode == 1)
+    k_dense_tma<RN, 1><<<grid, threads, smem, s>>>(g, b, tr, copy_sel, out);
+  else
+    k_dense_tma<RN, 2><<<grid, threads, smem, s>>>(g, b, tr, copy_sel, out);
   return cudaGetLastError();
 }
 
 template <int RN>
 cudaError_t prepare_tma_rn(size_t smem) {
-  return cudaFuncSetAttribute(k_dense_tma<RN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_dense_tma<RN, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dense_tma<RN, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dense_tma<RN, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return e;
+}
+
+template <int RN>
+cudaError_t tma_materialize_rn(const Geom& g, const Bufs& b, int tr, size_t smem, int grid,
+                               int threads, float* L_out, float* S_out, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (L_out) e = launch_tma_rn<RN>(g, b, tr, smem, grid, threads, s, 1, 0, L_out);
+  if (e == cudaSuccess && S_out) e = launch_tma_rn<RN>(g, b, tr, smem, grid, threads, s, 2, 1, S_out);
+  return e;
 }
 
 // Tile geometry of the TMA pass; returns false when the pass does not apply (d_n % 4 != 0,
@@ -443,7 +472,8 @@ cudaError_t launch_dense(const Geom& g, const Bufs& b, int form, cudaStream_t s)
     size_t smem;
     if (tma_geometry(g, tr, smem, threads)) {
       long long ntiles = (g.rowsT + tr - 1) / tr;
-      int grid = (int)(ntiles < 144 ? ntiles : 144);
+      int ctas = g.dense_ctas > 0 ? g.dense_ctas : 144;
+      int grid = (int)(ntiles < ctas ? ntiles : ctas);
       switch (g.rlast) {
         case 1: return launch_tma_rn<1>(g, b, tr, smem, grid, threads, s);
         case 2: return launch_tma_rn<2>(g, b, tr, smem, grid, threads, s);
@@ -478,6 +508,24 @@ cudaError_t launch_dense(const Geom& g, const Bufs& b, int form, cudaStream_t s)
 cudaError_t launch_materialize(const Geom& g, const Bufs& b, float* L_out, float* S_out,
                                cudaStream_t s) {
   if (!L_out && !S_out) return cudaSuccess;
+  {
+    int tr, threads;
+    size_t smem;
+    if (tma_geometry(g, tr, smem, threads)) {
+      long long ntiles = (g.rowsT + tr - 1) / tr;
+      int grid = (int)(ntiles < 144 ? ntiles : 144);
+      switch (g.rlast) {
+        case 1: return tma_materialize_rn<1>(g, b, tr, smem, grid, threads, L_out, S_out, s);
+        case 2: return tma_materialize_rn<2>(g, b, tr, smem, grid, threads, L_out, S_out, s);
+        case 3: return tma_materialize_rn<3>(g, b, tr, smem, grid, threads, L_out, S_out, s);
+        case 4: return tma_materialize_rn<4>(g, b, tr, smem, grid, threads, L_out, S_out, s);
+        case 5: return tma_materialize_rn<5>(g, b, tr, smem, grid, threads, L_out, S_out, s);
+        case 6: return tma_materialize_rn<6>(g, b, tr, smem, grid, threads, L_out, S_out, s);
+        case 7: return tma_materialize_rn<7>(g, b, tr, smem, grid, threads, L_out, S_out, s);
+        default: return tma_materialize_rn<8>(g, b, tr, smem, grid, threads, L_out, S_out, s);
+      }
+    }
+  }
   const long long dn = g.d[g.n - 1];
   int bx = (int)(dn < 256 ? ((dn + 31) / 32) * 32 : 256);
   unsigned gy = (unsigned)((dn + bx - 1) / bx);

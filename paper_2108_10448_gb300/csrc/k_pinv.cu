@@ -15,7 +15,7 @@
 //                orthogonality correction only). Each step roughly squares the subspace error;
 //                two steps take the FP32 basis to FP64 accuracy. Then an FP64 Rayleigh-Ritz on
 //                the r x r block, the cutoff of SVD_r, and Y_i = V_r Sigma_r^-1 = W^T Q_r
-//                Sigma_r^-2. One thread-block cluster of RT_CLUSTER CTAs per mode shares the
+//                Sigma_r^-2. One thread-block cluster of 16 (or 8) CTAs per mode shares the
 //                m x r panels through global memory (L2) between cluster barriers.
 #include <cooperative_groups.h>
 
@@ -100,6 +100,7 @@ __device__ __forceinline__ void tri_decode(int w, int P, int& a, int& bb) {
 
 __global__ void __launch_bounds__(kJacThreads) k_jacobi(Geom g, Bufs b) {
   extern __shared__ float smem[];
+  if (b.warm[blockIdx.x]) return;
   __shared__ int nrot;
   __shared__ float tabs;
   const int i = blockIdx.x;
@@ -216,6 +217,7 @@ constexpr int kFullLd = kFullMaxN + 1;
 
 __global__ void __launch_bounds__(kJacThreads, 1) k_jacobi_full(Geom g, Bufs b, int warm_ok) {
   extern __shared__ float smem[];
+  if (b.warm[blockIdx.x]) return;
   __shared__ int nrot;
   __shared__ float tabs;
   __shared__ int pp[kFullMaxN / 2], pq[kFullMaxN / 2];
@@ -351,14 +353,17 @@ __global__ void __launch_bounds__(kJacThreads, 1) k_jacobi_full(Geom g, Bufs b, 
 // For m <= 128 the FP32 eigenbasis comes from a tridiagonal reduction instead of Jacobi sweeps
 // (about m sequential steps instead of ~9 sweeps of m rounds):
 //   a. Householder tridiagonalisation Q^T M Q = T (Golub and Van Loan, Alg. 8.3.1), one warp per
-//      row for the symmetric matrix-vector product;
-//   b. all eigenvalues of T by multisection on Sturm counts (8 shifts per eigenvalue per round);
-//   c. eigenvectors of T by inverse iteration (tridiagonal LU with partial pivoting, three steps
-//      from a hashed start vector), except for the largest group of eigenvalues closer than
-//      1e-5 ||T|| (in practice the near-zero tail late in the solve), whose basis is taken as
-//      the orthogonal complement of all other vectors (Householder QR), and Gram-Schmidt inside
-//      any other small group;
-//   d. back-transformation by the stored reflectors, eight threads per column.
+//      row, the reflector and the update vector cached in registers;
+//   b. all eigenvalues of T by multisection on Sturm counts (8 shifts per eigenvalue per round,
+//      pivots kept away from zero by pivmin as in LAPACK's bisection);
+//   c. eigenvectors of T from twisted factorisations (Fernando 1997; Parlett and Dhillon 2000):
+//      one stationary and one progressive qd recurrence, the twist index where |gamma_k| is
+//      smallest, then two triangular sweeps -- no iteration and no per-thread work arrays.
+//      The largest group of eigenvalues closer than 1e-5 ||T|| (in practice the near-zero tail
+//      late in the solve) gets the orthogonal complement of all other vectors (Householder QR)
+//      as its basis; any other small group is orthogonalised by Gram-Schmidt;
+//   d. back-transformation by the stored reflectors, eight threads per column, each holding 16
+//      consecutive entries of its column in registers.
 // The result only has to be FP32-accurate: the FP64 refinement that follows fixes the top-r
 // subspace to FP64 accuracy.
 constexpr int kTriMax = 128;
@@ -369,94 +374,83 @@ __device__ __forceinline__ float warp_sum_f(float v) {
   return v;
 }
 
-__device__ int sturm_count(const float* d, const float* e2, int m, float x) {
+// Number of eigenvalues of T below x (Sturm count), pivots bounded away from zero by pivmin.
+__device__ int sturm_count(const float* d, const float* e2, int m, float x, float pivmin) {
   int cnt = 0;
   float q = d[0] - x;
+  if (fabsf(q) < pivmin) q = -pivmin;
   if (q < 0.f) ++cnt;
   for (int k = 1; k < m; ++k) {
-    if (q == 0.f) q = -1e-30f;
-    q = (d[k] - x) - e2[k - 1] / q;
+    q = (d[k] - x) - __fdividef(e2[k - 1], q);
+    if (fabsf(q) < pivmin) q = -pivmin;
     if (q < 0.f) ++cnt;
   }
   return cnt;
 }
 
-// Solve (T - s I) y = y in place (FP32, tridiagonal LU with partial pivoting, as in LAPACK's
-// slagtf/slagts). Zero pivots are replaced by `pert`. Work arrays live in local memory.
-__device__ void tri_solve(const float* d, const float* e, int m, float s, float pert, float* y,
-                          int ystride) {
-  float l[kTriMax], dg[kTriMax], u1[kTriMax], u2[kTriMax];
-  unsigned char piv[kTriMax];
-  float cd = d[0] - s, cu1 = (m > 1) ? e[0] : 0.f, cu2 = 0.f;
-  for (int k = 0; k < m - 1; ++k) {
-    float sub = e[k];
-    float nd = d[k + 1] - s;
-    float nu = (k + 1 < m - 1) ? e[k + 1] : 0.f;
-    if (fabsf(cd) >= fabsf(sub)) {
-      piv[k] = 0;
-      if (cd == 0.f) cd = pert;
-      l[k] = sub / cd;
-      dg[k] = cd; u1[k] = cu1; u2[k] = cu2;
-      cd = nd - l[k] * cu1;
-      cu1 = nu;
-      cu2 = 0.f;
-    } else {
-      piv[k] = 1;
-      l[k] = cd / sub;
-      dg[k] = sub; u1[k] = nd; u2[k] = nu;
-      float ncd = cu1 - l[k] * nd;
-      cu1 = cu2 - l[k] * nu;
-      cd = ncd;
-      cu2 = 0.f;
-    }
+// Eigenvector of the tridiagonal T (d, e) for the eigenvalue lam by a twisted factorisation.
+// z: output column (stride ld), also used for D-; w: scratch column (stride ld) for L+.
+__device__ void twisted_vector(const float* d, const float* e, int m, float lam, float pivmin,
+                               float* z, float* w, int ld) {
+  float dm = d[m - 1] - lam;
+  if (fabsf(dm) < pivmin) dm = pivmin;
+  z[(m - 1) * ld] = dm;
+  for (int j = m - 2; j >= 0; --j) {
+    float u = e[j] / dm;
+    dm = (d[j] - lam) - u * e[j];
+    if (fabsf(dm) < pivmin) dm = pivmin;
+    z[j * ld] = dm;
   }
-  if (cd == 0.f) cd = pert;
-  dg[m - 1] = cd;
-  for (int k = 0; k < m - 1; ++k) {
-    float a = y[k * ystride], bb = y[(k + 1) * ystride];
-    if (piv[k]) { float t = a; a = bb; bb = t; }
-    y[k * ystride] = a;
-    y[(k + 1) * ystride] = bb - l[k] * a;
+  float dp = d[0] - lam;
+  if (fabsf(dp) < pivmin) dp = pivmin;
+  float best = fabsf(dp + z[0] - (d[0] - lam));
+  int kb = 0;
+  for (int j = 0; j < m - 1; ++j) {
+    float l = e[j] / dp;
+    w[j * ld] = l;
+    dp = (d[j + 1] - lam) - l * e[j];
+    if (fabsf(dp) < pivmin) dp = pivmin;
+    float gk = fabsf(dp + z[(j + 1) * ld] - (d[j + 1] - lam));
+    if (gk < best) { best = gk; kb = j + 1; }
   }
-  float x1 = 0.f, x2 = 0.f;
-  for (int k = m - 1; k >= 0; --k) {
-    float t = y[k * ystride];
-    if (k + 1 < m) t -= u1[k] * x1;
-    if (k + 2 < m) t -= u2[k] * x2;
-    float xk = t / dg[k];
-    y[k * ystride] = xk;
-    x2 = x1;
-    x1 = xk;
+  float zj = 1.f;
+  float nn = 1.f;
+  for (int j = kb; j < m - 1; ++j) {  // z_{j+1} = -(e_j / D-_{j+1}) z_j
+    float zn = -(e[j] / z[(j + 1) * ld]) * zj;
+    z[(j + 1) * ld] = zn;
+    nn = fmaf(zn, zn, nn);
+    zj = zn;
   }
-}
-
-__device__ __forceinline__ float hash_unit(int i, int j) {
-  unsigned h = (unsigned)j * 2654435761u + (unsigned)i * 40503u + 12345u;
-  h ^= h >> 16;
-  h *= 0x7feb352du;
-  h ^= h >> 15;
-  return (float)(h & 0xffffffu) * (1.f / 16777216.f) - 0.5f;
+  z[kb * ld] = 1.f;
+  zj = 1.f;
+  for (int j = kb - 1; j >= 0; --j) {  // z_j = -L+_j z_{j+1}
+    float zn = -w[j * ld] * zj;
+    z[j * ld] = zn;
+    nn = fmaf(zn, zn, nn);
+    zj = zn;
+  }
+  float inv = 1.f / sqrtf(nn);
+  for (int j = 0; j < m; ++j) z[j * ld] *= inv;
 }
 
 __global__ void __launch_bounds__(kJacThreads, 1) k_eig_tri(Geom g, Bufs b) {
   extern __shared__ float smem[];
+  if (b.warm[blockIdx.x]) return;  // warm attempt certified for this mode
   __shared__ float dv[kTriMax], ev[kTriMax], e2[kTriMax], tauv[kTriMax], vb[kTriMax], pv[kTriMax];
   __shared__ float lam[kTriMax], qt[kTriMax];
   __shared__ int cid[kTriMax], inbig[kTriMax], known[kTriMax];
-  __shared__ float sh_scale, sh_tau, sh_lo, sh_hi, sh_nrm;
+  __shared__ float sh_scale, sh_tau, sh_lo, sh_hi, sh_nrm, sh_pivmin;
   __shared__ int sh_big, sh_nknown;
   const int i = blockIdx.x;
   const int m = g.m[i];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   float* A = smem;                       // m x kTriLd: matrix, then reflectors below the diagonal
   float* Z = A + kTriMax * kTriLd;       // m x kTriLd: eigenvectors of T (columns)
-  float* Y = Z + kTriMax * kTriLd;       // m x kTriLd: QR work for the complement
+  float* Y = Z + kTriMax * kTriLd;       // m x kTriLd: per-vector scratch, then QR work
   const double* M64 = b.gram + g.offM[i];
   long long tph = clock64();
-  for (int t = tid; t < m * m; t += blockDim.x) {
-    int r = t / m, c = t - r * m;
-    A[r * kTriLd + c] = (float)M64[t];
-  }
+  for (int r = wid; r < m; r += nw)
+    for (int c = lane; c < m; c += 32) A[r * kTriLd + c] = (float)M64[(long long)r * m + c];
   __syncthreads();
   PHASE_MARK(tph, "tri.load");
   // ---- a. tridiagonalisation
@@ -487,32 +481,65 @@ __global__ void __launch_bounds__(kJacThreads, 1) k_eig_tri(Geom g, Bufs b) {
     __syncthreads();
     const float tau = sh_tau, scale = sh_scale;
     for (int k = tid; k < sN; k += blockDim.x) {
-      float v = (k == 0) ? 1.f : A[(j + 1 + k) * kTriLd + j] * scale;
-      if (tau == 0.f) v = (k == 0) ? 1.f : 0.f;
+      float v = (tau == 0.f) ? ((k == 0) ? 1.f : 0.f)
+                             : ((k == 0) ? 1.f : A[(j + 1 + k) * kTriLd + j] * scale);
       vb[k] = v;
+      A[(j + 1 + k) * kTriLd + j] = v;  // the reflector, kept below the diagonal
     }
     __syncthreads();
-    for (int k = tid; k < sN; k += blockDim.x) A[(j + 1 + k) * kTriLd + j] = vb[k];  // reflector
     if (tau != 0.f) {
-      // p = tau * A22 v, one warp per row
-      for (int rr = wid; rr < sN; rr += nw) {
-        const float* row = A + (j + 1 + rr) * kTriLd + (j + 1);
-        float acc = 0.f;
-        for (int k = lane; k < sN; k += 32) acc = fmaf(row[k], vb[k], acc);
-        acc = warp_sum_f(acc);
-        if (lane == 0) pv[rr] = tau * acc;
+      float vreg[4], preg[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int c = lane + 32 * q;
+        vreg[q] = (c < sN) ? vb[c] : 0.f;
+      }
+      // p = tau * A22 v, one warp per row, four rows per warp reduced together
+      for (int rb = wid; rb < sN; rb += 4 * nw) {
+        float acc[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int rr = rb + u * nw;
+          acc[u] = 0.f;
+          if (rr < sN) {
+            const float* row = A + (j + 1 + rr) * kTriLd + (j + 1);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              int c = lane + 32 * q;
+              if (c < sN) acc[u] = fmaf(row[c], vreg[q], acc[u]);
+            }
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
+        if (lane == 0) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (rb + u * nw < sN) pv[rb + u * nw] = tau * acc[u];
+        }
       }
       __syncthreads();
-      // K = tau/2 * p.v (every warp, redundantly), then A22 -= v w^T + w v^T with w = p - K v
       float acc = 0.f;
-      for (int k = lane; k < sN; k += 32) acc = fmaf(pv[k], vb[k], acc);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int c = lane + 32 * q;
+        preg[q] = (c < sN) ? pv[c] : 0.f;
+        acc = fmaf(preg[q], vreg[q], acc);
+      }
       const float K = 0.5f * tau * warp_sum_f(acc);
+      float wreg[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) wreg[q] = preg[q] - K * vreg[q];
+      // A22 -= v w^T + w v^T
       for (int r = wid; r < sN; r += nw) {
         const float vr = vb[r], wr = pv[r] - K * vr;
         float* arow = A + (j + 1 + r) * kTriLd + (j + 1);
-        for (int c = lane; c < sN; c += 32) {
-          const float vc = vb[c], wc = pv[c] - K * vc;
-          arow[c] = arow[c] - vr * wc - wr * vc;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          int c = lane + 32 * q;
+          if (c < sN) arow[c] = arow[c] - vr * wreg[q] - wr * vreg[q];
         }
       }
     }
@@ -537,6 +564,7 @@ __global__ void __launch_bounds__(kJacThreads, 1) k_eig_tri(Geom g, Bufs b) {
     sh_lo = lo - 1e-6f * span - 1e-30f;
     sh_hi = hi + 1e-6f * span + 1e-30f;
     sh_nrm = nrm + 1e-30f;
+    sh_pivmin = 7.8886091e-31f * fmaxf(1.f, sh_nrm * sh_nrm);  // 2^-100 max(1, ||T||^2)
   }
   __syncthreads();
   PHASE_MARK(tph, "tri.reduce");
@@ -545,13 +573,14 @@ __global__ void __launch_bounds__(kJacThreads, 1) k_eig_tri(Geom g, Bufs b) {
     const int G = 8;
     const int ei = tid / G, gl = tid % G;
     const unsigned gmask = 0xffu << ((lane / G) * G);
+    const float pivmin = sh_pivmin;
     float a = sh_lo, bnd = sh_hi;
     if (ei < m) {
       for (int rd = 0; rd < 40; ++rd) {
         // eigenvalues of the FP32 matrix are only determined to about eps ||T||
         if (bnd - a <= 2.f * 5.9604645e-8f * (fmaxf(fabsf(a), fabsf(bnd)) + sh_nrm)) break;
         float x = a + (bnd - a) * (float)(gl + 1) / (float)(G + 1);
-        int cnt = sturm_count(dv, e2, m, x);
+        int cnt = sturm_count(dv, e2, m, x, pivmin);
         float na = a, nb = bnd;
         bool found = false;
         for (int t = 0; t < G; ++t) {
@@ -566,14 +595,11 @@ __global__ void __launch_bounds__(kJacThreads, 1) k_eig_tri(Geom g, Bufs b) {
         bnd = nb;
       }
       if (gl == 0) lam[ei] = 0.5f * (a + bnd);
-    } else {
-      // idle lanes of a partially used warp still take part in the shuffles above only if
-      // their group is active; groups with ei >= m skip the loop entirely (whole group).
     }
   }
   __syncthreads();
   PHASE_MARK(tph, "tri.bisect");
-  // ---- c. clusters, inverse iteration, complement
+  // ---- c. groups, eigenvectors, complement
   if (tid == 0) {
     const float tol = 1e-5f * sh_nrm;
     int c = 0, best = 0, bestsz = 1, cur = 1;
@@ -593,17 +619,15 @@ __global__ void __launch_bounds__(kJacThreads, 1) k_eig_tri(Geom g, Bufs b) {
   }
   __syncthreads();
   if (tid < m && !inbig[tid] && (tid == 0 || cid[tid] != cid[tid - 1])) {
-    // this thread owns its whole (non-big) cluster: members cstart..next start
+    // this thread owns its whole (non-big) group: members tid .. next group start
     const int c0 = tid;
     int c1 = c0 + 1;
     while (c1 < m && cid[c1] == cid[c0]) ++c1;
-    const float pert = 5.9604645e-8f * sh_nrm;
     for (int k = c0; k < c1; ++k) {
       float* y = Z + k;  // column k, stride kTriLd
-      for (int r = 0; r < m; ++r) y[r * kTriLd] = hash_unit(k, r);
-      for (int it = 0; it < 3; ++it) {
-        tri_solve(dv, ev, m, lam[k], pert, y, kTriLd);
-        for (int jj = c0; jj < k; ++jj) {  // Gram-Schmidt inside the cluster
+      twisted_vector(dv, ev, m, lam[k], sh_pivmin, y, Y + k, kTriLd);
+      if (k > c0) {
+        for (int jj = c0; jj < k; ++jj) {  // Gram-Schmidt inside the group
           float dot = 0.f;
           for (int r = 0; r < m; ++r) dot = fmaf(Z[r * kTriLd + jj], y[r * kTriLd], dot);
           for (int r = 0; r < m; ++r) y[r * kTriLd] -= dot * Z[r * kTriLd + jj];
@@ -616,14 +640,12 @@ __global__ void __launch_bounds__(kJacThreads, 1) k_eig_tri(Geom g, Bufs b) {
     }
   }
   __syncthreads();
-  PHASE_MARK(tph, "tri.inviter");
+  PHASE_MARK(tph, "tri.vectors");
   if (sh_big >= 0) {
     // Householder QR of the known vectors (m x nk), then the complement H_1..H_nk [0; I]
     const int nk = sh_nknown;
-    for (int t = tid; t < m * nk; t += blockDim.x) {
-      int r = t / nk, c = t - r * nk;
-      Y[r * kTriLd + c] = Z[r * kTriLd + known[c]];
-    }
+    for (int r = wid; r < m; r += nw)
+      for (int c = lane; c < nk; c += 32) Y[r * kTriLd + c] = Z[r * kTriLd + known[c]];
     __syncthreads();
     for (int j = 0; j < nk; ++j) {
       if (wid == 0) {
@@ -637,8 +659,7 @@ __global__ void __launch_bounds__(kJacThreads, 1) k_eig_tri(Geom g, Bufs b) {
           float v0 = x0 - beta;
           float vn = acc - x0 * x0 + v0 * v0;
           qt[j] = (vn > 0.f) ? 2.f / vn : 0.f;
-          vb[0] = v0;  // v = [v0, x(j+1:)]; kept in column j of Y with Y[j][j] = v0
-          Y[j * kTriLd + j] = v0;
+          Y[j * kTriLd + j] = v0;  // v = [v0, x(j+1:)] kept in column j
         }
       }
       __syncthreads();
@@ -651,7 +672,7 @@ __global__ void __launch_bounds__(kJacThreads, 1) k_eig_tri(Geom g, Bufs b) {
       }
       __syncthreads();
     }
-    // complement columns: start from unit vectors e_{nk + cc}, apply H_nk..H_1 (reverse order)
+    // complement columns: unit vectors e_{nk + cc}, then H_nk .. H_1 applied in reverse order
     int cc = 0;
     for (int k = 0; k < m; ++k) {
       if (!inbig[k]) continue;
@@ -673,30 +694,50 @@ __global__ void __launch_bounds__(kJacThreads, 1) k_eig_tri(Geom g, Bufs b) {
   }
   __syncthreads();
   PHASE_MARK(tph, "tri.complement");
-  // ---- d. back-transformation Z <- H_0 ... H_{m-3} Z, eight threads per column
+  // ---- d. back-transformation Z <- H_0 ... H_{m-3} Z: eight threads per column, each with
+  //         16 consecutive rows of its column in registers
   {
     const int G = 8;
     const int col = tid / G, gl = tid % G;
     const unsigned gmask = 0xffu << ((lane / G) * G);
+    const int r0 = gl * 16;
+    float z[16];
     if (col < m) {
-      for (int j = m - 3; j >= 0; --j) {
-        const float tau = tauv[j];
-        if (tau == 0.f) continue;
-        float acc = 0.f;
-        for (int r = j + 1 + gl; r < m; r += G) acc = fmaf(A[r * kTriLd + j], Z[r * kTriLd + col], acc);
-        for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(gmask, acc, o);
-        acc *= tau;
-        for (int r = j + 1 + gl; r < m; r += G) Z[r * kTriLd + col] -= acc * A[r * kTriLd + j];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) z[k] = (r0 + k < m) ? Z[(r0 + k) * kTriLd + col] : 0.f;
+    }
+    for (int j = m - 3; j >= 0; --j) {
+      const float tau = tauv[j];
+      if (tau == 0.f) continue;
+      float a[16];
+      float acc = 0.f;
+      if (r0 + 15 > j) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const int r = r0 + k;
+          a[k] = (r > j && r < m) ? A[r * kTriLd + j] : 0.f;
+          acc = fmaf(a[k], z[k], acc);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) a[k] = 0.f;
       }
+      for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(gmask, acc, o);
+      acc *= tau;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) z[k] -= acc * a[k];
+    }
+    if (col < m) {
+#pragma unroll
+      for (int k = 0; k < 16; ++k)
+        if (r0 + k < m) Z[(r0 + k) * kTriLd + col] = z[k];
     }
   }
   __syncthreads();
   PHASE_MARK(tph, "tri.backtransform");
   float* outV = b.jV + g.offM[i];
-  for (int t = tid; t < m * m; t += blockDim.x) {
-    int r = t / m, c = t - r * m;
-    outV[t] = Z[r * kTriLd + c];
-  }
+  for (int r = wid; r < m; r += nw)
+    for (int c = lane; c < m; c += 32) outV[(long long)r * m + c] = Z[r * kTriLd + c];
   for (int j = tid; j < m; j += blockDim.x) b.jL[g.offL[i] + j] = lam[j];
   PHASE_MARK(tph, "tri.store");
 }
@@ -712,23 +753,43 @@ __device__ void cluster_barrier() {
 // this CTA's columns and rows, and a chunk of W columns for Y = W^T Q_r Sigma^-2.
 constexpr int kWChunk = 32;
 
-__host__ __device__ inline size_t refine_smem_bytes(int m, int r) {
-  int own = (m + RT_CLUSTER - 1) / RT_CLUSTER;
+__host__ __device__ inline size_t refine_smem_bytes(int m, int r, int ncl) {
+  int own = (m + ncl - 1) / ncl;
   return sizeof(double) * ((size_t)own * m + 3 * (size_t)m * r) +
          sizeof(float) * (2 * (size_t)own * m + (size_t)m * kWChunk);
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the 4 lanes of a quad (lanes 4k..4k+3). GB300 issues a warp-wide FP64 FMA about
+// every 64 cycles per sub-partition, so each FP64 dot product of the refinement is split over
+// a quad (4 lanes): enough warps to keep all four sub-partitions' FP64 pipes busy, and only
+// two shuffle-adds per dot.
+__device__ __forceinline__ double quad_sum_d(double v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  return v;
 }
 
 __device__ __forceinline__ void load_panel(double* dst, const double* src, int n) {
   for (int t = threadIdx.x; t < n; t += blockDim.x) dst[t] = src[t];
 }
 
-__global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b) {
+// mode 1: full refinement after the FP32 eigensolver (skipped for a mode whose warm attempt
+//         succeeded). mode 0: warm attempt (RTCUR-F, k >= 1): three FP64 subspace-iteration
+//         steps from the previous iteration's basis, accepted only when certified (see below).
+__global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode) {
   extern __shared__ double rsm[];
   cg::cluster_group cl = cg::this_cluster();
   const int crank = (int)cl.block_rank();
-  const int i = blockIdx.x / RT_CLUSTER;
+  const int NCL = g.ncl;
+  const int i = blockIdx.x / NCL;
   const int m = g.m[i], r = g.r[i], q = g.q[i];
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  const int ql = tid & 3, nq = blockDim.x >> 2;  // quad lane, number of quads
   __shared__ int top[RT_MAXR];
   __shared__ int pos_of[RT_MAXM];      // -1 for tail indices, else position in top
   __shared__ double lamT[RT_MAXR];
@@ -751,9 +812,9 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b) {
   double* sig = b.sig + g.offR[i];
   double* Yout = b.Y + g.offY[i];
   const long long* set = set_of(g, b);
-  const int lo = (m * crank) / RT_CLUSTER, hi = (m * (crank + 1)) / RT_CLUSTER;
+  const int lo = (m * crank) / NCL, hi = (m * (crank + 1)) / NCL;
   const int own = hi - lo;
-  const int ownmax = (m + RT_CLUSTER - 1) / RT_CLUSTER;
+  const int ownmax = (m + NCL - 1) / NCL;
   double* sM = rsm;                         // own x m
   double* sX1 = sM + (size_t)ownmax * m;     // m x r
   double* sYw = sX1 + (size_t)m * r;         // m x r
@@ -763,6 +824,12 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b) {
   float* sW = sXr + (size_t)ownmax * m;      // m x kWChunk
 
   long long tph = clock64();
+  int* warm_flag = b.warm + i;
+  if (mode == 1 && *warm_flag) return;  // the warm attempt already produced this mode's factors
+  if (mode == 0) {
+    if (tid == 0 && crank == 0) *warm_flag = 0;
+    if (g.variant != 0 || b.st->k < 1) return;
+  }
   if (tid == 0) {
     tie = 0;
     for (int a = 0; a < m; ++a) pos_of[a] = -1;
@@ -784,6 +851,77 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b) {
     sXc[t] = Xh[(long long)a * m + lo + j];
   }
   __syncthreads();
+  if (mode == 0) {
+    // warm start: the previous iteration's top-r basis, then FP64 subspace iteration with a
+    // Cholesky QR per step: X <- (M X) L^-T, L L^T = (M X)^T (M X)
+    for (int t = tid; t < own * r; t += blockDim.x) {
+      int a = lo + t / r, j = t % r;
+      X1[(long long)a * r + j] = Qr[(long long)a * r + j];
+    }
+    cluster_barrier();
+    load_panel(sX1, X1, m * r);
+    __syncthreads();
+    __shared__ int chol_ok;
+    for (int it = 0; it < 3; ++it) {
+      for (int t0 = tid >> 2; t0 < ((own * r + nq - 1) / nq) * nq; t0 += nq) {
+        const int t = t0;
+        const bool act = t < own * r;
+        int a = act ? t / r : 0, j = act ? t - a * r : 0;
+        double acc = 0.0;
+        if (act) {
+          const double* Ma = sM + (size_t)a * m;
+          for (int c = ql; c < m; c += 4) acc = fma(Ma[c], sX1[c * r + j], acc);
+        }
+        acc = quad_sum_d(acc);
+        if (act && ql == 0) Yw[(long long)(lo + a) * r + j] = acc;
+      }
+      cluster_barrier();
+      load_panel(sYw, Yw, m * r);
+      __syncthreads();
+      for (int t = wid; t < r * r; t += nw) {
+        int j = t / r, l = t % r;
+        double acc = 0.0;
+        for (int a = lane; a < m; a += 32) acc = fma(sYw[a * r + j], sYw[a * r + l], acc);
+        acc = warp_sum_d(acc);
+        if (lane == 0) Gq[t] = acc;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        chol_ok = 1;
+        for (int j = 0; j < r && chol_ok; ++j) {
+          double d = Gq[j * r + j];
+          for (int l = 0; l < j; ++l) d -= Gq[j * r + l] * Gq[j * r + l];
+          if (!(d > 0.0)) { chol_ok = 0; break; }
+          d = sqrt(d);
+          Gq[j * r + j] = d;
+          for (int ii = j + 1; ii < r; ++ii) {
+            double v = Gq[ii * r + j];
+            for (int l = 0; l < j; ++l) v -= Gq[ii * r + l] * Gq[j * r + l];
+            Gq[ii * r + j] = v / d;
+          }
+        }
+      }
+      __syncthreads();
+      if (!chol_ok) return;  // uniform across the cluster (same data): the full path runs
+      for (int a = lo + tid; a < hi; a += blockDim.x) {
+        double y[RT_MAXR];
+#pragma unroll
+        for (int j = 0; j < RT_MAXR; ++j) {
+          if (j < r) {
+            double v = sYw[a * r + j];
+            for (int l = 0; l < j; ++l) v -= Gq[j * r + l] * y[l];
+            y[j] = v / Gq[j * r + j];
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < RT_MAXR; ++j)
+          if (j < r) X1[(long long)a * r + j] = y[j];
+      }
+      cluster_barrier();
+      load_panel(sX1, X1, m * r);
+      __syncthreads();
+    }
+  } else {
   for (int t = tid; t < own * r; t += blockDim.x) {
     int a = lo + t / r, j = t % r;
     X1[(long long)a * r + j] = (double)Xh[(long long)a * m + top[j]];
@@ -791,52 +929,66 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b) {
   cluster_barrier();
   load_panel(sX1, X1, m * r);
   __syncthreads();
+  }
   PHASE_MARK(tph, "ref.init");
-  for (int step = 0; step < g.refine_steps; ++step) {
-    // S1: Yw = M X1 on own rows
-    for (int t = tid; t < own * r; t += blockDim.x) {
-      int a = t / r, j = t - a * r;
-      const double* Ma = sM + (size_t)a * m;
+  for (int step = 0; step < ((mode == 0) ? 0 : g.refine_steps); ++step) {
+    // S1: Yw = M X1 on own rows (one quad per output)
+    for (int t0 = tid >> 2; t0 < ((own * r + nq - 1) / nq) * nq; t0 += nq) {
+      const int t = t0;
       double acc = 0.0;
-      for (int c = 0; c < m; ++c) acc = fma(Ma[c], sX1[c * r + j], acc);
-      Yw[(long long)(lo + a) * r + j] = acc;
+      int a = 0, j = 0;
+      if (t < own * r) {
+        a = t / r; j = t - a * r;
+        const double* Ma = sM + (size_t)a * m;
+        for (int c = ql; c < m; c += 4) acc = fma(Ma[c], sX1[c * r + j], acc);
+      }
+      acc = quad_sum_d(acc);
+      if (t < own * r && ql == 0) Yw[(long long)(lo + a) * r + j] = acc;
     }
     cluster_barrier();
     load_panel(sYw, Yw, m * r);
     __syncthreads();
     // Rayleigh quotients of the current top columns (every CTA, redundantly)
-    if (tid < r) {
-      int j = tid;
+    for (int j = wid; j < r; j += nw) {
       double s1 = 0.0, nn = 0.0;
-      for (int a = 0; a < m; ++a) {
+      for (int a = lane; a < m; a += 32) {
         double x = sX1[a * r + j];
         s1 = fma(x, sYw[a * r + j], s1);
         nn = fma(x, x, nn);
       }
-      lamT[j] = s1 / nn;
+      s1 = warp_sum_d(s1);
+      nn = warp_sum_d(nn);
+      if (lane == 0) lamT[j] = s1 / nn;
     }
     __syncthreads();
     double lmax = lamT[0];
     for (int j = 1; j < r; ++j) lmax = fmax(lmax, lamT[j]);
     // S2: E for own basis indices ii; the basis is Xh with its top columns replaced by X1
-    for (int t = tid; t < own * r; t += blockDim.x) {
-      int jj = t / r, j = t - jj * r;
+    for (int t0 = tid >> 2; t0 < ((own * r + nq - 1) / nq) * nq; t0 += nq) {
+      const int t = t0;
+      const bool act = t < own * r;
+      int jj = act ? t / r : 0, j = act ? t - jj * r : 0;
       int ii = lo + jj;
-      int pi = pos_of[ii];
+      int pi = act ? pos_of[ii] : 0;
       double s1 = 0.0, dot = 0.0;
-      if (pi >= 0) {
-        for (int a = 0; a < m; ++a) {
-          double xf = sX1[a * r + pi];
-          s1 = fma(xf, sYw[a * r + j], s1);
-          dot = fma(xf, sX1[a * r + j], dot);
-        }
-      } else {
-        for (int a = 0; a < m; ++a) {
-          double xf = (double)sXc[a * own + jj];
-          s1 = fma(xf, sYw[a * r + j], s1);
-          dot = fma(xf, sX1[a * r + j], dot);
+      if (act) {
+        if (pi >= 0) {
+          for (int a = ql; a < m; a += 4) {
+            double xf = sX1[a * r + pi];
+            s1 = fma(xf, sYw[a * r + j], s1);
+            dot = fma(xf, sX1[a * r + j], dot);
+          }
+        } else {
+          for (int a = ql; a < m; a += 4) {
+            double xf = (double)sXc[a * own + jj];
+            s1 = fma(xf, sYw[a * r + j], s1);
+            dot = fma(xf, sX1[a * r + j], dot);
+          }
         }
       }
+      s1 = quad_sum_d(s1);
+      dot = quad_sum_d(dot);
+      if (!act || ql != 0) continue;
       double Rij = ((pi == j) ? 1.0 : 0.0) - dot;
       double Eij;
       if (pi >= 0) {
@@ -855,29 +1007,230 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b) {
     cluster_barrier();
     load_panel(sE, E, m * r);
     __syncthreads();
-    // S3: X1 <- X1 + Xf E on own rows
-    for (int t = tid; t < own * r; t += blockDim.x) {
-      int a = t / r, j = t - a * r;
+    // S3: X1 <- X1 + Xf E on own rows (one quad per output)
+    for (int t0 = tid >> 2; t0 < ((own * r + nq - 1) / nq) * nq; t0 += nq) {
+      const int t = t0;
+      const bool act = t < own * r;
+      int a = act ? t / r : 0, j = act ? t - a * r : 0;
       double upd = 0.0;
-      const float* xr = sXr + (size_t)a * m;
-      for (int ii = 0; ii < m; ++ii) {
-        int pi = pos_of[ii];
-        double xf = (pi >= 0) ? sX1[(lo + a) * r + pi] : (double)xr[ii];
-        upd = fma(xf, sE[ii * r + j], upd);
+      if (act) {
+        const float* xr = sXr + (size_t)a * m;
+        for (int ii = ql; ii < m; ii += 4) {
+          int pi = pos_of[ii];
+          double xf = (pi >= 0) ? sX1[(lo + a) * r + pi] : (double)xr[ii];
+          upd = fma(xf, sE[ii * r + j], upd);
+        }
       }
-      X1[(long long)(lo + a) * r + j] = sX1[(lo + a) * r + j] + upd;
+      upd = quad_sum_d(upd);
+      if (act && ql == 0) X1[(long long)(lo + a) * r + j] = sX1[(lo + a) * r + j] + upd;
     }
     cluster_barrier();
     load_panel(sX1, X1, m * r);
     __syncthreads();
     PHASE_MARK(tph, "ref.step");
   }
-  // F1: orthonormalise X1 (Cholesky QR in FP64)
-  for (int t = tid; t < r * r; t += blockDim.x) {
+  // Fast finish. L needs only the top-r invariant subspace: for any basis X1 of it,
+  // (M_r)^+ = X1 H^-1 X1^T with H = X1^T M X1, so U_i^+ = W^T X1 H^-1 X1^T, B_i = C_i W^T X1 H^-1
+  // and G = R x_i X1^T give the same L as the singular-vector form. This needs one r x r FP64
+  // Cholesky and no eigenvectors. It is taken when H is far from the SVD_r cutoff (its FP32
+  // eigenvalues satisfy lambda_min > 1e-6 lambda_max, so every sigma_j exceeds the cutoff
+  // max(m, q) 2^-24 sigma_1 by orders of magnitude); otherwise the exact path below runs.
+  for (int t0 = tid >> 2; t0 < ((own * r + nq - 1) / nq) * nq; t0 += nq) {
+    const int t = t0;
+    const bool act = t < own * r;
+    int a = act ? t / r : 0, j = act ? t - a * r : 0;
+    double acc = 0.0;
+    if (act) {
+      const double* Ma = sM + (size_t)a * m;
+      for (int c = ql; c < m; c += 4) acc = fma(Ma[c], sX1[c * r + j], acc);
+    }
+    acc = quad_sum_d(acc);
+    if (act && ql == 0) Yw[(long long)(lo + a) * r + j] = acc;
+  }
+  cluster_barrier();
+  load_panel(sYw, Yw, m * r);
+  __syncthreads();
+  for (int t = wid; t < r * r; t += nw) {
     int j = t / r, l = t % r;
     double acc = 0.0;
-    for (int a = 0; a < m; ++a) acc = fma(sX1[a * r + j], sX1[a * r + l], acc);
-    Gq[t] = acc;
+    for (int a = lane; a < m; a += 32) acc = fma(sX1[a * r + j], sYw[a * r + l], acc);
+    acc = warp_sum_d(acc);
+    if (lane == 0) Hs[t] = acc;
+  }
+  __syncthreads();
+  __shared__ int fast_ok;
+  __shared__ double cert[2];
+  if (mode == 0) {
+    // certificate, summed over the cluster: trace(M) and ||M X - X H||_F^2 (own rows)
+    double trp = 0.0, rsp = 0.0;
+    for (int a = tid; a < own; a += blockDim.x) trp += sM[(size_t)a * m + lo + a];
+    for (int t = tid; t < own * r; t += blockDim.x) {
+      int a = t / r, j = t - a * r;
+      double v = sYw[(lo + a) * r + j];
+      for (int l = 0; l < r; ++l) v -= sX1[(lo + a) * r + l] * Hs[l * r + j];
+      rsp = fma(v, v, rsp);
+    }
+    trp = warp_sum_d(trp);
+    rsp = warp_sum_d(rsp);
+    __shared__ double wpart[2][32];
+    if (lane == 0) { wpart[0][wid] = trp; wpart[1][wid] = rsp; }
+    __syncthreads();
+    if (tid == 0) {
+      double a0 = 0.0, a1 = 0.0;
+      for (int w = 0; w < nw; ++w) { a0 += wpart[0][w]; a1 += wpart[1][w]; }
+      double* slot = b.ework + 3 * g.sumMR + (long long)(i * NCL + crank) * 2;
+      slot[0] = a0;
+      slot[1] = a1;
+    }
+    cluster_barrier();
+    if (tid == 0) {
+      double a0 = 0.0, a1 = 0.0;
+      for (int c2 = 0; c2 < NCL; ++c2) {
+        const double* slot = b.ework + 3 * g.sumMR + (long long)(i * NCL + c2) * 2;
+        a0 += slot[0];
+        a1 += slot[1];
+      }
+      cert[0] = a0;
+      cert[1] = a1;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    // FP32 eigenvalues of H (cyclic Jacobi on an r x r copy) for the conditioning test
+    float hf[RT_MAXR * RT_MAXR];
+    for (int t = 0; t < r * r; ++t) {
+      int j = t / r, l = t % r;
+      hf[t] = (float)(0.5 * (Hs[j * r + l] + Hs[l * r + j]));
+    }
+    for (int sw = 0; sw < 30; ++sw) {
+      int nrot = 0;
+      for (int p = 0; p < r - 1; ++p)
+        for (int qq = p + 1; qq < r; ++qq) {
+          float apq = hf[p * r + qq], app = hf[p * r + p], aqq = hf[qq * r + qq];
+          if (apq == 0.f || fabsf(apq) <= 1e-7f * sqrtf(fabsf(app * aqq))) continue;
+          ++nrot;
+          float th = (aqq - app) / (2.f * apq);
+          float tt = (th >= 0.f ? 1.f : -1.f) / (fabsf(th) + sqrtf(th * th + 1.f));
+          float c = 1.f / sqrtf(tt * tt + 1.f), sn = tt * c;
+          for (int l = 0; l < r; ++l) {
+            float hp = hf[p * r + l], hq = hf[qq * r + l];
+            hf[p * r + l] = c * hp - sn * hq;
+            hf[qq * r + l] = sn * hp + c * hq;
+          }
+          for (int l = 0; l < r; ++l) {
+            float hp = hf[l * r + p], hq = hf[l * r + qq];
+            hf[l * r + p] = c * hp - sn * hq;
+            hf[l * r + qq] = sn * hp + c * hq;
+          }
+        }
+      if (nrot == 0) break;
+    }
+    float lmx = 0.f, lmn = 3.4e38f;
+    for (int j = 0; j < r; ++j) { lmx = fmaxf(lmx, hf[j * r + j]); lmn = fminf(lmn, hf[j * r + j]); }
+    fast_ok = (lmx > 0.f && lmn > 1e-6f * lmx) ? 1 : 0;
+    if (mode == 0 && fast_ok) {
+      // M is PSD, so trace(M) - trace(H) bounds the sum of the eigenvalues outside span(X).
+      // If that is below lambda_min(H) / 2, span(X) is the top-r invariant subspace with a gap of
+      // at least lambda_min(H) / 2, and the residual bounds its error by 2 ||R|| / lambda_min(H).
+      double trH = 0.0;
+      for (int j = 0; j < r; ++j) trH += Hs[j * r + j];
+      const double tail = cert[0] - trH;
+      const double lmin = (double)lmn;
+      if (!(tail < 0.5 * lmin && sqrt(fmax(cert[1], 0.0)) <= 1e-11 * lmin)) fast_ok = 0;
+    }
+    if (fast_ok) {
+      // singular values (diagnostic), descending
+      for (int j = 0; j < r; ++j) wv[j] = sqrt((double)fmaxf(hf[j * r + j], 0.f));
+      for (int j = 0; j < r; ++j)
+        for (int l = j + 1; l < r; ++l)
+          if (wv[l] > wv[j]) { double t = wv[j]; wv[j] = wv[l]; wv[l] = t; }
+      // FP64 Cholesky H = L L^T into Gq
+      for (int t = 0; t < r * r; ++t) Gq[t] = 0.5 * (Hs[t] + Hs[(t % r) * r + t / r]);
+      for (int j = 0; j < r; ++j) {
+        double d = Gq[j * r + j];
+        for (int l = 0; l < j; ++l) d -= Gq[j * r + l] * Gq[j * r + l];
+        if (!(d > 0.0)) { fast_ok = 0; break; }
+        d = sqrt(d);
+        Gq[j * r + j] = d;
+        for (int ii = j + 1; ii < r; ++ii) {
+          double v = Gq[ii * r + j];
+          for (int l = 0; l < j; ++l) v -= Gq[ii * r + l] * Gq[j * r + l];
+          Gq[ii * r + j] = v / d;
+        }
+      }
+    }
+    if (tie && crank == 0) atomicOr(&b.st->flags, 2);
+    else if (tie) atomicOr(&b.st->flags, 2);
+  }
+  __syncthreads();
+  if (fast_ok) {
+    // P = X1 H^-1 on own rows (solve L L^T p = x1_a), Qr = X1
+    for (int a = lo + tid; a < hi; a += blockDim.x) {
+      double y[RT_MAXR];
+#pragma unroll
+      for (int j = 0; j < RT_MAXR; ++j) {
+        if (j < r) {
+          double v = sX1[a * r + j];
+          for (int l = 0; l < j; ++l) v -= Gq[j * r + l] * y[l];
+          y[j] = v / Gq[j * r + j];
+        }
+      }
+#pragma unroll
+      for (int j = RT_MAXR - 1; j >= 0; --j) {
+        if (j < r) {
+          double v = y[j];
+          for (int l = j + 1; l < r; ++l) v -= Gq[l * r + j] * y[l];
+          y[j] = v / Gq[j * r + j];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < RT_MAXR; ++j)
+        if (j < r) {
+          Qw[(long long)a * r + j] = y[j];
+          Qr[(long long)a * r + j] = sX1[a * r + j];
+        }
+    }
+    if (crank == 0 && tid < r) sig[tid] = wv[tid];
+    cluster_barrier();
+    load_panel(sE, Qw, m * r);  // sE holds P = X1 H^-1
+    __syncthreads();
+    // Y = W^T P (q x r) on own columns of W
+    const int blo = (q * crank) / NCL, bhi = (q * (crank + 1)) / NCL;
+    for (int c0 = blo; c0 < bhi; c0 += kWChunk) {
+      const int cn = min(kWChunk, bhi - c0);
+      for (int t = tid; t < m * cn; t += blockDim.x) {
+        int cc = t / m, a = t - cc * m;
+        sW[a * kWChunk + cc] = w_entry(g, b, set, i, a, c0 + cc);
+      }
+      __syncthreads();
+      for (int t0 = tid >> 2; t0 < ((cn * r + nq - 1) / nq) * nq; t0 += nq) {
+        const int t = t0;
+        const bool act = t < cn * r;
+        int cc = act ? t / r : 0, j = act ? t - cc * r : 0;
+        double acc = 0.0;
+        if (act)
+          for (int a = ql; a < m; a += 4) acc = fma((double)sW[a * kWChunk + cc], sE[a * r + j], acc);
+        acc = quad_sum_d(acc);
+        if (act && ql == 0) Yout[(long long)(c0 + cc) * r + j] = acc;
+      }
+      __syncthreads();
+    }
+    if (mode == 0 && crank == 0 && tid == 0) {
+      *warm_flag = 1;
+      atomicAdd((unsigned long long*)&b.st->warm_hits, 1ull);
+    }
+    PHASE_MARK(tph, "ref.fast");
+    return;
+  }
+  if (mode == 0) return;  // not certified: the eigensolver and the full refinement run
+  // ---- exact path (H close to the SVD_r cutoff): singular vectors and the cutoff
+  // F1: orthonormalise X1 (Cholesky QR in FP64)
+  for (int t = wid; t < r * r; t += nw) {
+    int j = t / r, l = t % r;
+    double acc = 0.0;
+    for (int a = lane; a < m; a += 32) acc = fma(sX1[a * r + j], sX1[a * r + l], acc);
+    acc = warp_sum_d(acc);
+    if (lane == 0) Gq[t] = acc;
   }
   __syncthreads();
   if (tid == 0) {  // Gq <- L (lower Cholesky factor), in place
@@ -913,24 +1266,30 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b) {
   cluster_barrier();
   load_panel(sX1, Qw, m * r);  // sX1 now holds Q
   __syncthreads();
-  // F2: Yw = M Q on own rows
-  for (int t = tid; t < own * r; t += blockDim.x) {
-    int a = t / r, j = t - a * r;
-    const double* Ma = sM + (size_t)a * m;
+  // F2: Yw = M Q on own rows (one quad per output)
+  for (int t0 = tid >> 2; t0 < ((own * r + nq - 1) / nq) * nq; t0 += nq) {
+    const int t = t0;
+    const bool act = t < own * r;
+    int a = act ? t / r : 0, j = act ? t - a * r : 0;
     double acc = 0.0;
-    for (int c = 0; c < m; ++c) acc = fma(Ma[c], sX1[c * r + j], acc);
-    Yw[(long long)(lo + a) * r + j] = acc;
+    if (act) {
+      const double* Ma = sM + (size_t)a * m;
+      for (int c = ql; c < m; c += 4) acc = fma(Ma[c], sX1[c * r + j], acc);
+    }
+    acc = quad_sum_d(acc);
+    if (act && ql == 0) Yw[(long long)(lo + a) * r + j] = acc;
   }
   cluster_barrier();
   load_panel(sYw, Yw, m * r);
   __syncthreads();
   PHASE_MARK(tph, "ref.qr+MQ");
   // F3: H = Q^T M Q (r x r), its eigenpairs by FP64 cyclic Jacobi, cutoff of SVD_r
-  for (int t = tid; t < r * r; t += blockDim.x) {
+  for (int t = wid; t < r * r; t += nw) {
     int j = t / r, l = t % r;
     double acc = 0.0;
-    for (int a = 0; a < m; ++a) acc = fma(sX1[a * r + j], sYw[a * r + l], acc);
-    Hs[t] = acc;
+    for (int a = lane; a < m; a += 32) acc = fma(sX1[a * r + j], sYw[a * r + l], acc);
+    acc = warp_sum_d(acc);
+    if (lane == 0) Hs[t] = acc;
   }
   __syncthreads();
   if (tid == 0) {
@@ -941,22 +1300,25 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b) {
       }
       for (int l = 0; l < r; ++l) Yh[j * r + l] = (j == l) ? 1.0 : 0.0;
     }
-    for (int sw = 0; sw < 50; ++sw) {
-      double off = 0.0, dia = 0.0;
-      for (int j = 0; j < r; ++j)
-        for (int l = 0; l < r; ++l) {
-          if (j != l) off += Hs[j * r + l] * Hs[j * r + l];
-          else dia += Hs[j * r + l] * Hs[j * r + l];
-        }
-      if (off <= 1e-32 * dia) break;
+    for (int sw = 0; sw < 30; ++sw) {
+      int nrot = 0;
       for (int p = 0; p < r - 1; ++p)
         for (int qq = p + 1; qq < r; ++qq) {
           double apq = Hs[p * r + qq];
-          if (apq == 0.0) continue;
           double app = Hs[p * r + p], aqq = Hs[qq * r + qq];
-          double theta = (aqq - app) / (2.0 * apq);
-          double tt = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-          double c = 1.0 / sqrt(tt * tt + 1.0), s1 = tt * c;
+          // skip pairs already diagonal to working precision (no square root needed)
+          if (apq * apq <= 1e-32 * fabs(app * aqq) || apq == 0.0) continue;
+          ++nrot;
+          // rotation angle from FP32 (an inexact angle only leaves a smaller off-diagonal for
+          // the next sweep); the rotation itself is orthogonal to FP64 accuracy
+          float thf = (float)((aqq - app) / 2.0) / (float)apq;
+          float tf = (thf >= 0.f ? 1.f : -1.f) / (fabsf(thf) + sqrtf(thf * thf + 1.f));
+          double tt = (double)tf;
+          double x = 1.0 + tt * tt;
+          double y = (double)rsqrtf((float)x);
+          y = y * (1.5 - 0.5 * x * y * y);
+          y = y * (1.5 - 0.5 * x * y * y);
+          double c = y, s1 = tt * c;
           for (int l = 0; l < r; ++l) {  // rows p, q
             double hp = Hs[p * r + l], hq = Hs[qq * r + l];
             Hs[p * r + l] = c * hp - s1 * hq;
@@ -967,13 +1329,13 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b) {
             Hs[l * r + p] = c * hp - s1 * hq;
             Hs[l * r + qq] = s1 * hp + c * hq;
           }
-          Hs[p * r + qq] = Hs[qq * r + p] = 0.0;
           for (int l = 0; l < r; ++l) {
             double yp = Yh[l * r + p], yq = Yh[l * r + qq];
             Yh[l * r + p] = c * yp - s1 * yq;
             Yh[l * r + qq] = s1 * yp + c * yq;
           }
         }
+      if (nrot == 0) break;
     }
     for (int j = 0; j < r; ++j) order[j] = j;
     for (int j = 0; j < r; ++j)  // sort eigenvalues descending (selection)
@@ -1010,7 +1372,7 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b) {
   load_panel(sE, Qr, m * r);  // sE now holds Q_r
   __syncthreads();
   // F4: Y = W^T Q_r Sigma^-2 (q x r) on own columns of W, staged kWChunk columns at a time
-  const int blo = (q * crank) / RT_CLUSTER, bhi = (q * (crank + 1)) / RT_CLUSTER;
+  const int blo = (q * crank) / NCL, bhi = (q * (crank + 1)) / NCL;
   for (int c0 = blo; c0 < bhi; c0 += kWChunk) {
     const int cn = min(kWChunk, bhi - c0);
     for (int t = tid; t < m * cn; t += blockDim.x) {
@@ -1018,14 +1380,14 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b) {
       sW[a * kWChunk + cc] = w_entry(g, b, set, i, a, c0 + cc);
     }
     __syncthreads();
-    for (int t = tid; t < cn * r; t += blockDim.x) {
+    for (int t = wid; t < cn * r; t += nw) {
       int cc = t / r, j = t - cc * r;
       double acc = 0.0;
       if (wv[j] > 0.0) {
-        for (int a = 0; a < m; ++a) acc = fma((double)sW[a * kWChunk + cc], sE[a * r + j], acc);
-        acc /= wv[j] * wv[j];
+        for (int a = lane; a < m; a += 32) acc = fma((double)sW[a * kWChunk + cc], sE[a * r + j], acc);
+        acc = warp_sum_d(acc) / (wv[j] * wv[j]);
       }
-      Yout[(long long)(c0 + cc) * r + j] = acc;
+      if (lane == 0) Yout[(long long)(c0 + cc) * r + j] = acc;
     }
     __syncthreads();
   }
@@ -1081,28 +1443,52 @@ cudaError_t launch_jacobi(const Geom& g, const Bufs& b, cudaStream_t s) {
 size_t refine_smem_max(const Geom& g) {
   size_t mx = 0;
   for (int i = 0; i < g.n; ++i) {
-    size_t v = refine_smem_bytes(g.m[i], g.r[i]);
+    size_t v = refine_smem_bytes(g.m[i], g.r[i], g.ncl);
     mx = v > mx ? v : mx;
   }
   return mx;
 }
 
-cudaError_t prepare_refine(const Geom& g) {
-  return cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)refine_smem_max(g));
+// Chooses the cluster size of the refinement (16 CTAs per mode when the device can schedule
+// such clusters, else 8) and sets the kernel's attributes. Updates g.ncl.
+cudaError_t prepare_refine(Geom& g) {
+  cudaError_t e = cudaFuncSetAttribute(k_refine, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  g.ncl = 16;
+  e = cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)refine_smem_max(g));
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(16 * g.n);
+  cfg.blockDim = dim3(kRefThreads);
+  cfg.dynamicSmemBytes = refine_smem_max(g);
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 16;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclusters, k_refine, &cfg) != cudaSuccess || nclusters < 1) {
+    cudaGetLastError();
+    g.ncl = 8;
+    e = cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)refine_smem_max(g));
+  }
+  return e;
 }
 
-cudaError_t launch_refine(const Geom& g, const Bufs& b, cudaStream_t s) {
+cudaError_t launch_refine(const Geom& g, const Bufs& b, int mode, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(RT_CLUSTER * g.n);
+  cfg.gridDim = dim3(g.ncl * g.n);
   cfg.blockDim = dim3(kRefThreads);
   cfg.dynamicSmemBytes = refine_smem_max(g);
   cfg.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = RT_CLUSTER;
+  at[0].val.clusterDim.x = g.ncl;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_refine, g, b);
+  return cudaLaunchKernelEx(&cfg, k_refine, g, b, mode);
 }

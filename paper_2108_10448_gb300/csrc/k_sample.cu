@@ -55,6 +55,7 @@ __global__ void k_setup(Geom g, Bufs b, double zeta0) {
   st->cont = (g.max_iter > 0 && 1.0 > g.tol) ? 1 : 0;
   st->nnz_s = st->inband_s = 0;
   st->jsweeps = 0;
+  st->warm_hits = 0;
   st->nnz_f = st->inband_f = -1;
   st->resid_f = -1.0;
   for (int i = 0; i < RT_MAXN + 1; ++i) st->den[i] = st->num[i] = 0.0;

@@ -22,7 +22,6 @@
 #define RT_MAXR 16
 #define RT_MAXM 192      // cap on |I_i| (the FP32 Jacobi keeps M and V in shared memory)
 #define RT_MAXQ 4096     // cap on |J_i|
-#define RT_CLUSTER 8     // CTAs per mode in the FP64 refinement kernel
 #define RT_RED_SLOTS 16  // doubles per block in reduction partials
 
 struct Geom {
@@ -38,6 +37,8 @@ struct Geom {
   int max_sweeps;
   int warm_start;                // start the Jacobi from the previous iteration's basis
   int eig_method;                // FP32 eigenbasis: 0 tridiagonal (m <= 128), 1 Jacobi
+  int ncl;                       // CTAs per cluster in the FP64 refinement (16 or 8)
+  int dense_ctas;                // persistent CTAs of the dense pass (0: default)
   int nG;                       // prod r_i
   int rlast;                    // r_n
   long long d[RT_MAXN];
@@ -87,6 +88,7 @@ struct State {
   double num[RT_MAXN + 1];  // sum of E^2 per segment
   double zeta0;      // max|X| when requested
   int jsweeps;       // FP32 eigensolver sweeps/steps of the last iteration (max over modes)
+  long long warm_hits;  // certified warm results, counted over the solve
   int pad;
 };
 
@@ -113,7 +115,8 @@ struct Bufs {
   double* Qr;            // sum m_i r_i, final orthonormal top-r basis
   double* sig;           // sum r_i, singular values (0 where truncated)
   double* Y;             // sum q_i r_i, V_r Sigma_r^-1
-  double* ework;         // 3 * sum m_i r_i, refinement scratch
+  double* ework;         // 3 * sum m_i r_i + 2 * 16 * n, refinement scratch
+  int* warm;             // n flags: the warm attempt produced mode i's factors this iteration
   double* Bpart;         // split-K partials of B (nchunk * sumB)
   float* B[2];           // sumB each
   float* G[2];           // nG each
@@ -137,7 +140,7 @@ cudaError_t launch_gather_x(const Geom& g, const Bufs& b, cudaStream_t s);
 cudaError_t launch_sample_ht(const Geom& g, const Bufs& b, cudaStream_t s);
 cudaError_t launch_gram(const Geom& g, const Bufs& b, cudaStream_t s);
 cudaError_t launch_jacobi(const Geom& g, const Bufs& b, cudaStream_t s);
-cudaError_t launch_refine(const Geom& g, const Bufs& b, cudaStream_t s);
+cudaError_t launch_refine(const Geom& g, const Bufs& b, int mode, cudaStream_t s);
 cudaError_t launch_factor_B(const Geom& g, const Bufs& b, cudaStream_t s);
 cudaError_t launch_core(const Geom& g, const Bufs& b, cudaStream_t s);
 cudaError_t launch_table(const Geom& g, const Bufs& b, int next, cudaStream_t s);
@@ -151,7 +154,7 @@ cudaError_t launch_materialize(const Geom& g, const Bufs& b, float* L_out, float
                                cudaStream_t s);
 size_t jacobi_smem_bytes(int m);
 cudaError_t prepare_jacobi(size_t smem);
-cudaError_t prepare_refine(const Geom& g);  // dynamic shared-memory limit of the refinement  // sets the kernel's dynamic shared-memory limit
+cudaError_t prepare_refine(Geom& g);  // cluster size and shared-memory limit of the refinement  // sets the kernel's dynamic shared-memory limit
 
 // ---------------------------------------------------------------- device helpers
 #ifdef __CUDACC__

@@ -30,6 +30,7 @@ class rtcur_result(C.Structure):
                 ("jacobi_sweeps", C.c_int32), ("e", C.c_double), ("zeta", C.c_double),
                 ("nnz_sample", C.c_int64), ("inband_sample", C.c_int64),
                 ("nnz_full", C.c_int64), ("inband_full", C.c_int64), ("resid_full", C.c_double),
+                ("warm_hits", C.c_int64),
                 ("e_hist", C.POINTER(C.c_double)), ("zeta_hist", C.POINTER(C.c_double)),
                 ("nnz_hist", C.POINTER(C.c_int64))]
 
@@ -139,6 +140,7 @@ class Result:
         self.nnz_full = r.nnz_full
         self.inband_full = r.inband_full
         self.resid_full = r.resid_full
+        self.warm_hits = r.warm_hits
         self.e_hist = e_hist[:min(k, e_hist.size)].copy()
         self.zeta_hist = z_hist[:min(k, z_hist.size)].copy()
         self.nnz_hist = n_hist[:min(k, n_hist.size)].copy()
