@@ -11,7 +11,6 @@
 // whole solve runs on the device with one host synchronisation at the end.
 #include <cmath>
 #include <cstdarg>
-#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -218,7 +217,7 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
   g.max_sweeps = o.jacobi_max_sweeps;
   g.warm_start = 0;
   g.eig_method = o.eig_method;
-  { const char* ev = getenv("RTCUR_DENSE_CTAS"); g.dense_ctas = ev ? atoi(ev) : 0; }
+  g.dense_ctas = 0;
   g.gamma = gamma;
   g.tol = tol;
   g.inband = o.inband_rel;
@@ -329,6 +328,10 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
   AL(b.e_hist, max_iter);
   AL(b.z_hist, max_iter);
   AL(b.nnz_hist, max_iter);
+#ifdef RTCUR_TIMELINE
+  AL(b.tl, 4096);
+  AL(b.tl_n, 1);
+#endif
   if (o.scope == RTCUR_SCOPE_FULL) AL(p->S_internal, g.N);
 #undef AL
   // the latency-bound sampled chain is captured from a high-priority stream, the bandwidth-bound
@@ -480,6 +483,22 @@ rtcur_status rtcur_get_factors(rtcur_plan* p, float* G, float* B, int32_t* k, do
 }
 
 int64_t rtcur_sample_count(const rtcur_plan* p) { return p ? p->g.nS : 0; }
+
+#ifdef RTCUR_TIMELINE
+// Diagnostic builds only: copy out the kernel timeline and reset it.
+RTCUR_API int rtcur_debug_timeline(rtcur_plan* p, unsigned long long* out, int max_rec) {
+  unsigned n = 0;
+  cudaDeviceSynchronize();
+  cudaMemcpy(&n, p->b.tl_n, sizeof n, cudaMemcpyDeviceToHost);
+  if (n > 4096) n = 4096;
+  if ((int)n > max_rec) n = (unsigned)max_rec;
+  std::vector<TlRec> h(n);
+  cudaMemcpy(h.data(), p->b.tl, sizeof(TlRec) * n, cudaMemcpyDeviceToHost);
+  for (unsigned i = 0; i < n; ++i) { out[3 * i] = h[i].id; out[3 * i + 1] = h[i].t0; out[3 * i + 2] = h[i].t1; }
+  cudaMemset(p->b.tl_n, 0, sizeof(unsigned));
+  return (int)n;
+}
+#endif
 
 const char* rtcur_last_error(const rtcur_plan* p) { return p ? p->err.c_str() : g_create_err.c_str(); }
 

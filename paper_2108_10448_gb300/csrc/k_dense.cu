@@ -181,6 +181,18 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsig
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
+// 1-D bulk copy of streamed data with an L2 evict-first policy: the tensor passes through L2
+// once, so it should not push out the small working set of the concurrent sampled chain.
+__device__ __forceinline__ void bulk_g2s_stream(void* dst, const void* src, unsigned bytes,
+                                                unsigned long long* bar) {
+  unsigned long long pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+      : "memory");
+}
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
                                          unsigned long long* bar) {
   asm volatile(
@@ -196,6 +208,7 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
 //         `out` (zero when k = 0). Modes 1 and 2 materialise the solve's outputs.
 template <int RN, int MODE>
 __global__ void __launch_bounds__(1024, 1) k_dense_tma(Geom g, Bufs b, int tr, int copy_sel, float* out) {
+  TL_BEGIN();
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ unsigned long long full[kStages];
   __shared__ double sh[32];
@@ -252,7 +265,7 @@ __global__ void __launch_bounds__(1024, 1) k_dense_tma(Geom g, Bufs b, int tr, i
         long long a0 = (r0 * RN) & ~3LL, a1 = ((r0 + nr) * RN + 3) & ~3LL;
         unsigned tbytes = (unsigned)((a1 - a0) * 4);
         mbar_expect_tx(&full[s], bytes + tbytes);
-        if (bytes) bulk_g2s(ring + (size_t)s * stage_f4, X + r0 * dn, bytes, &full[s]);
+        if (bytes) bulk_g2s_stream(ring + (size_t)s * stage_f4, X + r0 * dn, bytes, &full[s]);
         bulk_g2s(tring + (size_t)s * tstage, T + a0, tbytes, &full[s]);
         issued[s] = 1;
       }
@@ -314,7 +327,7 @@ __global__ void __launch_bounds__(1024, 1) k_dense_tma(Geom g, Bufs b, int tr, i
         long long a0 = (rn0 * RN) & ~3LL, a1 = ((rn0 + nr2) * RN + 3) & ~3LL;
         unsigned tbytes = (unsigned)((a1 - a0) * 4);
         mbar_expect_tx(&full[s], bytes + tbytes);
-        if (bytes) bulk_g2s(ring + (size_t)s * stage_f4, X + rn0 * dn, bytes, &full[s]);
+        if (bytes) bulk_g2s_stream(ring + (size_t)s * stage_f4, X + rn0 * dn, bytes, &full[s]);
         bulk_g2s(tring + (size_t)s * tstage, T + a0, tbytes, &full[s]);
 #pragma unroll
         for (int s2 = 0; s2 < kStages; ++s2) issued[s2] += (s2 == s) ? 1 : 0;
@@ -357,6 +370,7 @@ __global__ void __launch_bounds__(1024, 1) k_dense_tma(Geom g, Bufs b, int tr, i
     }
     if (threadIdx.x == 0) b.ticket[TK_DENSE] = 0u;
   }
+  TL_END(1 + 20 * MODE);
 }
 
 template <int RN>
@@ -371,11 +385,18 @@ cudaError_t launch_tma_rn(const Geom& g, const Bufs& b, int tr, size_t smem, int
   return cudaGetLastError();
 }
 
+// The pass streams its data, so it gives L1 away: the SMs it runs on are configured with the
+// maximum shared-memory carveout, which leaves room beside its ring for the concurrent sampled
+// chain's blocks (a smaller carveout would make them wait for the pass to finish).
 template <int RN>
 cudaError_t prepare_tma_rn(size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(k_dense_tma<RN, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dense_tma<RN, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dense_tma<RN, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaSuccess;
+  void* fns[3] = {(void*)k_dense_tma<RN, 0>, (void*)k_dense_tma<RN, 1>, (void*)k_dense_tma<RN, 2>};
+  for (void* f : fns) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  }
   return e;
 }
 
@@ -393,7 +414,7 @@ cudaError_t tma_materialize_rn(const Geom& g, const Bufs& b, int tr, size_t smem
 bool tma_geometry(const Geom& g, int& tr, size_t& smem, int& threads) {
   const long long dn = g.d[g.n - 1];
   if (dn % 4 != 0 || dn > 4096 || g.rlast > 8) return false;
-  long long t = 32768 / (dn * 4);
+  long long t = 32768 / (dn * 4);  // ~32 KB tiles, kStages deep
   if (t < 1) t = 1;
   if (t > g.rowsT) t = g.rowsT;
   tr = (int)t;

@@ -15,6 +15,7 @@ constexpr int kChunk = 32;   // b-columns per split-K partial of B_i = C_i Y_i
 
 // B partials: block -> (mode, t-block, chunk); thread -> row t.
 __global__ void __launch_bounds__(kThreads) k_factor_B_partial(Geom g, Bufs b) {
+  TL_BEGIN();
   int blk = blockIdx.x, i = 0;
   int tblocks = 0, chunks = 0;
   for (; i < g.n; ++i) {
@@ -44,10 +45,12 @@ __global__ void __launch_bounds__(kThreads) k_factor_B_partial(Geom g, Bufs b) {
 #pragma unroll
   for (int c = 0; c < RT_MAXR; ++c)
     if (c < r) out[c] = acc[c];
+  TL_END(6);
 }
 
 // B_next = sum of the partials in chunk order (deterministic), rounded to FP32.
 __global__ void __launch_bounds__(kThreads) k_factor_B_reduce(Geom g, Bufs b) {
+  TL_BEGIN();
   long long e = (long long)blockIdx.x * kThreads + threadIdx.x;
   if (e >= g.sumB) return;
   int i = 0;
@@ -56,12 +59,14 @@ __global__ void __launch_bounds__(kThreads) k_factor_B_reduce(Geom g, Bufs b) {
   double acc = 0.0;
   for (int ch = 0; ch < chunks; ++ch) acc += b.Bpart[(long long)ch * g.sumB + e];
   b.B[(b.st->k + 1) & 1][e] = (float)acc;
+  TL_END(7);
 }
 
 // One stage of G = R x_{n-1} Q^T ... x_0 Q^T (modes contracted from last to first).
 // Before stage s the modes j' > j = n-1-s already have size r, the others m. Q_j (m_j x r_j,
 // FP64) is staged in shared memory; each thread forms one output as an FP64 dot product.
 __global__ void __launch_bounds__(kThreads) k_core_stage(Geom g, Bufs b, int s, long long nout) {
+  TL_BEGIN();
   __shared__ double Qs[RT_MAXM * RT_MAXR];
   const int n = g.n;
   const int j = n - 1 - s;
@@ -106,11 +111,13 @@ __global__ void __launch_bounds__(kThreads) k_core_stage(Geom g, Bufs b, int s, 
   } else {
     b.Z[s & 1][o] = acc;
   }
+  TL_END(8);
 }
 
 // Table stage A: H[c_0, p_1..p_{n-2}, c_{n-1}] = sum over c_1..c_{n-2} of
 // G[c_0, c_1, .., c_{n-1}] prod_l B_l[p_l, c_l]   (H = G when n = 2).
 __global__ void __launch_bounds__(kThreads) k_table_A(Geom g, Bufs b, int next) {
+  TL_BEGIN();
   long long o = (long long)blockIdx.x * kThreads + threadIdx.x;
   if (o >= g.nH) return;
   const int n = g.n;
@@ -149,10 +156,12 @@ __global__ void __launch_bounds__(kThreads) k_table_A(Geom g, Bufs b, int next) 
     acc = fma((double)G[gidx], prod, acc);
   }
   b.H[o] = (float)acc;
+  TL_END(9);
 }
 
 // Table stage B: T[p_0, rest] = sum_{c_0} B_0[p_0, c_0] H[c_0, rest], FP32 FMA in ascending c_0.
 __global__ void __launch_bounds__(kThreads) k_table_B(Geom g, Bufs b, int next) {
+  TL_BEGIN();
   const long long rest = g.nH / g.r[0];
   long long o = (long long)blockIdx.x * kThreads + threadIdx.x;
   if (o >= g.d[0] * rest) return;
@@ -162,6 +171,7 @@ __global__ void __launch_bounds__(kThreads) k_table_B(Geom g, Bufs b, int next) 
   float acc = 0.f;
   for (int c = 0; c < g.r[0]; ++c) acc = fmaf(B0[p0 * g.r[0] + c], b.H[c * rest + w], acc);
   b.T[cp][o] = acc;
+  TL_END(10);
 }
 
 inline int nblocks(long long work) { return (int)((work + kThreads - 1) / kThreads); }

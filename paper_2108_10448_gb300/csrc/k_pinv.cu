@@ -44,6 +44,7 @@ __device__ __forceinline__ const long long* set_of(const Geom& g, const Bufs& b)
 
 // ------------------------------------------------------------------ 1. FP64 Gram matrix
 __global__ void __launch_bounds__(kGramTile * kGramTile) k_gram(Geom g, Bufs b) {
+  TL_BEGIN();
   __shared__ float wa[kGramTile][kGramChunk + 1];
   __shared__ float wb[kGramTile][kGramChunk + 1];
   // locate (mode, tile) for this block: per mode nt(nt+1)/2 lower-triangle tiles
@@ -80,6 +81,7 @@ __global__ void __launch_bounds__(kGramTile * kGramTile) k_gram(Geom g, Bufs b) 
     M[(long long)ra * m + rb] = acc;
     M[(long long)rb * m + ra] = acc;
   }
+  TL_END(3);
 }
 
 // ------------------------------------------------------------------ 2. FP32 Jacobi
@@ -434,6 +436,7 @@ __device__ void twisted_vector(const float* d, const float* e, int m, float lam,
 }
 
 __global__ void __launch_bounds__(kJacThreads, 1) k_eig_tri(Geom g, Bufs b) {
+  TL_BEGIN();
   extern __shared__ float smem[];
   if (b.warm[blockIdx.x]) return;  // warm attempt certified for this mode
   __shared__ float dv[kTriMax], ev[kTriMax], e2[kTriMax], tauv[kTriMax], vb[kTriMax], pv[kTriMax];
@@ -740,6 +743,7 @@ __global__ void __launch_bounds__(kJacThreads, 1) k_eig_tri(Geom g, Bufs b) {
     for (int c = lane; c < m; c += 32) outV[(long long)r * m + c] = Z[r * kTriLd + c];
   for (int j = tid; j < m; j += blockDim.x) b.jL[g.offL[i] + j] = lam[j];
   PHASE_MARK(tph, "tri.store");
+  TL_END(5);
 }
 
 // ------------------------------------------------------------------ 3. FP64 refinement
@@ -782,6 +786,7 @@ __device__ __forceinline__ void load_panel(double* dst, const double* src, int n
 //         succeeded). mode 0: warm attempt (RTCUR-F, k >= 1): three FP64 subspace-iteration
 //         steps from the previous iteration's basis, accepted only when certified (see below).
 __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode) {
+  TL_BEGIN();
   extern __shared__ double rsm[];
   cg::cluster_group cl = cg::this_cluster();
   const int crank = (int)cl.block_rank();
@@ -1392,6 +1397,7 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
     __syncthreads();
   }
   PHASE_MARK(tph, "ref.Y");
+  TL_END(4 + 10 * mode);
 }
 
 }  // namespace
@@ -1458,12 +1464,12 @@ cudaError_t prepare_refine(Geom& g) {
   e = cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)refine_smem_max(g));
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(16 * g.n);
+  cfg.gridDim = dim3(g.ncl * g.n);
   cfg.blockDim = dim3(kRefThreads);
   cfg.dynamicSmemBytes = refine_smem_max(g);
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = 16;
+  at[0].val.clusterDim.x = g.ncl;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;

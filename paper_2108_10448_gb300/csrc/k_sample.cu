@@ -117,6 +117,7 @@ __device__ __forceinline__ int segment_of(const Geom& g, long long e) {
 }
 
 __global__ void __launch_bounds__(kThreads) k_sample_ht(Geom g, Bufs b) {
+  TL_BEGIN();
   __shared__ double sh[kThreads / 32];
   const State* st = b.st;
   const int k = st->k;
@@ -205,9 +206,11 @@ __global__ void __launch_bounds__(kThreads) k_sample_ht(Geom g, Bufs b) {
       b.ticket[TK_SAMPLE] = 0u;
     }
   }
+  TL_END(2);
 }
 
 __global__ void __launch_bounds__(kThreads) k_sample_err(Geom g, Bufs b) {
+  TL_BEGIN();
   __shared__ double sh[kThreads / 32];
   const State* st = b.st;
   const int k = st->k;
@@ -251,9 +254,11 @@ __global__ void __launch_bounds__(kThreads) k_sample_err(Geom g, Bufs b) {
       b.ticket[TK_ERR] = 0u;
     }
   }
+  TL_END(11);
 }
 
 __global__ void k_commit(Geom g, Bufs b, unsigned long long handle, int use_handle) {
+  TL_BEGIN();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   State* st = b.st;
   int k = st->k;
@@ -270,6 +275,7 @@ __global__ void k_commit(Geom g, Bufs b, unsigned long long handle, int use_hand
   int cont = (e > g.tol) && (k + 1 < g.max_iter) && (st->err == 0);
   st->cont = cont;
   if (use_handle) cudaGraphSetConditional((cudaGraphConditionalHandle)handle, cont ? 1u : 0u);
+  TL_END(12);
 }
 
 __global__ void k_gate(Bufs b, unsigned long long handle) {

@@ -99,6 +99,8 @@ struct SolvePtrs {
   float* S;          // dense S^(k+1) (FULL scope); may be null in SAMPLED scope
 };
 
+struct TlRec { int id; int pad; unsigned long long t0, t1; };  // diagnostic timeline record
+
 struct Bufs {
   State* st;
   SolvePtrs* sp;
@@ -128,6 +130,8 @@ struct Bufs {
   double* e_hist;        // max_iter
   double* z_hist;        // max_iter
   long long* nnz_hist;   // max_iter
+  TlRec* tl;             // diagnostic timeline (null unless built with -DRTCUR_TIMELINE)
+  unsigned* tl_n;
 };
 
 enum { TK_SAMPLE = 0, TK_ERR = 1, TK_DENSE = 2, TK_MAXABS = 3, TK_COUNT = 8 };
@@ -172,6 +176,26 @@ cudaError_t prepare_refine(Geom& g);  // cluster size and shared-memory limit of
   } while (0)
 #else
 #define PHASE_MARK(t0, name) do { (void)t0; } while (0)
+#endif
+// Diagnostic timeline (compiled in only with -DRTCUR_TIMELINE): block 0, thread 0 of a kernel
+// appends (id, globaltimer at entry, globaltimer at exit) to a device log.
+#ifdef RTCUR_TIMELINE
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+#define TL_BEGIN() unsigned long long tl_t0_ = gtimer()
+#define TL_END(kid_)                                                               \
+  do {                                                                             \
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && b.tl) {          \
+      unsigned i_ = atomicAdd(b.tl_n, 1u);                                         \
+      if (i_ < 4096) { b.tl[i_].id = kid_; b.tl[i_].t0 = tl_t0_; b.tl[i_].t1 = gtimer(); } \
+    }                                                                              \
+  } while (0)
+#else
+#define TL_BEGIN() do { } while (0)
+#define TL_END(kid_) do { } while (0)
 #endif
 __device__ __forceinline__ int cur_copy(const State* st) { return st->k & 1; }
 
