@@ -89,6 +89,7 @@ cudaError_t capture_body(rtcur_plan* p, cudaStream_t s, unsigned long long handl
   if ((e = launch_factor_B(g, b, s)) != cudaSuccess) return e;
   if ((e = launch_core(g, b, s)) != cudaSuccess) return e;
   if ((e = launch_table(g, b, 1, s)) != cudaSuccess) return e;
+  if (full && p->opt.dense_form == RTCUR_FORM_FP32_PLAIN && (e = launch_plain_prep(g, b, s)) != cudaSuccess) return e;
   if ((e = launch_sample_err(g, b, s)) != cudaSuccess) return e;
   if (full && (e = cudaStreamWaitEvent(s, p->evJoin, 0)) != cudaSuccess) return e;
   return launch_commit(g, b, handle, use_handle, s);
@@ -182,7 +183,7 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
     }
   }
   if (o.scope != RTCUR_SCOPE_SAMPLED && o.scope != RTCUR_SCOPE_FULL) return fail(nullptr, RTCUR_EINVAL, "scope must be SAMPLED or FULL");
-  if (o.dense_form != RTCUR_FORM_FP32) return fail(nullptr, RTCUR_EINVAL, "dense_form %d is not available in this build", o.dense_form);
+  if (o.dense_form < RTCUR_FORM_FP32 || o.dense_form > RTCUR_FORM_TF32) return fail(nullptr, RTCUR_EINVAL, "dense_form must be 0..3");
   if (o.refine_steps < 0 || o.refine_steps > 8) return fail(nullptr, RTCUR_EINVAL, "refine_steps must be in [0, 8]");
   if (o.jacobi_max_sweeps < 1 || o.jacobi_max_sweeps > 100) return fail(nullptr, RTCUR_EINVAL, "jacobi_max_sweeps must be in [1, 100]");
   if (!(o.inband_rel >= 0.0 && o.inband_rel < 1.0)) return fail(nullptr, RTCUR_EINVAL, "inband_rel must be in [0, 1)");
@@ -250,6 +251,14 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
   }
   g.sumB = oB;
   g.sumMR = oQ;
+  g.dense_form = o.dense_form;
+  {
+    long long oDM = 0;
+    for (int i = 0; i < n_modes; ++i) { g.offDM[i] = oDM; oDM += g.d[i] * g.m[i]; }
+    g.sumDM = oDM;
+  }
+  if (o.scope == RTCUR_SCOPE_FULL && !dense_form_supported(g, o.dense_form))
+    return fail(nullptr, RTCUR_EINVAL, "dense_form %d does not support these dims/ranks (plain: 3 modes; BF16: d_n %% 8 == 0, d_n <= 1024, r_n <= 5; TF32: r_n <= 8)", o.dense_form);
   {
     long long oD = 0, oW = 0;
     for (int i = 0; i < n_modes; ++i) {
@@ -333,6 +342,15 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
   AL(b.tl_n, 1);
 #endif
   if (o.scope == RTCUR_SCOPE_FULL) AL(p->S_internal, g.N);
+  if (o.scope == RTCUR_SCOPE_FULL && o.dense_form == RTCUR_FORM_FP32_PLAIN) {
+    AL(b.Ap[0], g.sumDM);
+    AL(b.Ap[1], g.sumDM);
+    AL(b.Rp[0], g.nR);
+    AL(b.Rp[1], g.nR);
+    AL(b.Z1p, (long long)g.m[0] * g.m[1] * g.d[2]);
+    AL(b.Z2p, (long long)g.m[0] * g.d[1] * g.d[2]);
+    AL(b.Lplain, g.N);
+  }
 #undef AL
   // the latency-bound sampled chain is captured from a high-priority stream, the bandwidth-bound
   // dense pass from a low-priority one (kernel nodes keep their stream's priority)
@@ -390,6 +408,10 @@ rtcur_status rtcur_begin(rtcur_plan* p, const float* X, const int64_t* idx, floa
   CKC(p, cudaMemsetAsync(b.B[0], 0, sizeof(float) * g.sumB, s));
   CKC(p, cudaMemsetAsync(b.G[0], 0, sizeof(float) * g.nG, s));
   CKC(p, cudaMemsetAsync(b.warm, 0, sizeof(int) * RT_MAXN, s));
+  if (b.Ap[0]) {
+    CKC(p, cudaMemsetAsync(b.Ap[0], 0, sizeof(float) * g.sumDM, s));
+    CKC(p, cudaMemsetAsync(b.Rp[0], 0, sizeof(float) * g.nR, s));
+  }
   CKC(p, launch_setup(g, b, p->zeta0, p->zeta0 <= 0.0 ? 1 : 0, s));
   if (g.variant == RTCUR_VARIANT_F) CKC(p, launch_gather_x(g, b, s));
   p->X = X;

@@ -39,6 +39,7 @@ struct Geom {
   int eig_method;                // FP32 eigenbasis: 0 tridiagonal (m <= 128), 1 Jacobi
   int ncl;                       // CTAs per cluster in the FP64 refinement (16 or 8)
   int dense_ctas;                // persistent CTAs of the dense pass (0: default)
+  int dense_form;                // RTCUR_FORM_* of the dense pass
   int nG;                       // prod r_i
   int rlast;                    // r_n
   long long d[RT_MAXN];
@@ -61,6 +62,8 @@ struct Geom {
   long long offD[RT_MAXN];      // offsets of per-mode d_i arrays (position tables)
   long long offW[RT_MAXN];      // offsets of the compact W_i = C_i(I_i, :) (m_i x q_i)
   long long sumW;               // sum m_i q_i
+  long long offDM[RT_MAXN];     // offsets of A_i = B_i Q_i^T (d_i x m_i) in the plain form
+  long long sumDM;              // sum d_i m_i
   long long nchunk;             // split-K chunks of the B_i product (max over modes)
   long long sumB;               // sum d_i r_i
   long long nH;                 // size of the T stage-A table
@@ -130,6 +133,11 @@ struct Bufs {
   double* e_hist;        // max_iter
   double* z_hist;        // max_iter
   long long* nnz_hist;   // max_iter
+  float* Ap[2];          // plain form: A_i = B_i Q_i^T of L^(k), two copies
+  float* Rp[2];          // plain form: R of L^(k), two copies
+  float* Z1p;            // plain form: R x_3 A_3
+  float* Z2p;            // plain form: R x_3 A_3 x_2 A_2
+  float* Lplain;         // plain form: the materialised L^(k)
   TlRec* tl;             // diagnostic timeline (null unless built with -DRTCUR_TIMELINE)
   unsigned* tl_n;
 };
@@ -154,6 +162,9 @@ cudaError_t launch_commit(const Geom& g, const Bufs& b, unsigned long long handl
 cudaError_t launch_gate(const Bufs& b, unsigned long long handle, cudaStream_t s);
 cudaError_t launch_dense(const Geom& g, const Bufs& b, int form, cudaStream_t s);
 cudaError_t prepare_dense(const Geom& g);  // kernel attributes of the dense pass (call at create)
+bool dense_form_supported(const Geom& g, int form);
+cudaError_t launch_plain_dense(const Geom& g, const Bufs& b, cudaStream_t s);
+cudaError_t launch_plain_prep(const Geom& g, const Bufs& b, cudaStream_t s);
 cudaError_t launch_materialize(const Geom& g, const Bufs& b, float* L_out, float* S_out,
                                cudaStream_t s);
 size_t jacobi_smem_bytes(int m);

@@ -1,0 +1,50 @@
+"""Dense-pass forms (FULL scope) on the GPU: FP32 fused, FP32 plain (literal chain, unfused),
+BF16 (3-term split on tensor cores) and TF32 (tensor cores).
+
+The CUR iterates read only sampled entries, so every form must give the same iteration count,
+e^(k) history and L as the FP32 form. The whole-tensor S may differ only where |X - L| lies within
+the form's evaluation error of zeta: the relative error of L is about 2^-24 r (FP32 plain and
+fused orders differ), ~2^-16 for the BF16 split (the dropped lo*lo term) and ~2^-11 for TF32; the
+bands below are those bounds times a safety factor, relative to max |L|."""
+import numpy as np
+import pytest
+
+from paper_2108_10448_gb300 import rtcur as rt
+from paper_2108_10448_gb300 import synth
+
+from gpu_helpers import run_gpu
+
+pytestmark = pytest.mark.gpu
+
+BAND = {rt.FORM_FP32_PLAIN: 2e-6, rt.FORM_BF16: 1e-4, rt.FORM_TF32: 4e-3}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as ge
+    ge.build()
+
+
+@pytest.mark.parametrize("form", [rt.FORM_FP32_PLAIN, rt.FORM_BF16, rt.FORM_TF32])
+def test_form_matches_fp32_form(form):
+    p = synth.make_tucker_problem((48, 40, 64), (3, 3, 4), 0.1, 3, seed=21, max_iter=40)
+    sets = synth.draw_index_sets(p.dims, p.m, p.q, seed=21)
+    ref, L0, S0 = run_gpu(p, sets, "F", scope=rt.SCOPE_FULL, max_iter=40)
+    res, L1, S1 = run_gpu(p, sets, "F", scope=rt.SCOPE_FULL, max_iter=40, dense_form=form)
+    assert res.iters == ref.iters
+    np.testing.assert_array_equal(res.e_hist, ref.e_hist)
+    np.testing.assert_array_equal(L1, L0)
+    # S^(k) = HT_{zeta_k}(X - L^(k-1)): support differences only inside the form's band
+    diff = (S1 != 0) != (S0 != 0)
+    # where exactly one form kept an entry, its S value is X - L there: |X - L| is known
+    absD = np.where(S0 != 0, np.abs(S0), np.abs(S1))
+    zeta = ref.zeta
+    band = BAND[form] * np.max(np.abs(L0))
+    assert np.all(np.abs(absD[diff] - zeta) <= band + 1e-6 * zeta), int(diff.sum())
+    assert diff.sum() <= 1e-3 * diff.size
+
+
+def test_tensor_core_forms_reject_unsupported_shapes():
+    with pytest.raises(rt.RTCURError):
+        rt.rtcur_create([20, 20, 30], [2, 2, 2], [8, 8, 8], [16, 16, 16], 1.0, 0.7, 1e-5, 5, 0,
+                        rt.make_options(scope=rt.SCOPE_FULL, dense_form=rt.FORM_BF16))
