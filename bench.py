@@ -30,6 +30,16 @@ sys.path.insert(0, ROOT)
 METRIC = "RTCUR iters/s & time-to-1e-5 at 800³ rank 5: BF16/TF32 vs FP32 plain, % HBM roofline"
 
 
+# DRAM bytes (read + write) per launch of the FP32 fused dense pass, from one ncu capture of the
+# 400^3 pass (dram__bytes_read.sum 259.3 MB + dram__bytes_write.sum 201.0 MB) scaled by the
+# element count to 800^3. The write counter undercounts: up to the L2 size of S is still dirty in
+# L2 when the captured launch ends. Must be dropped whenever the kernel changes.
+DENSE_TRAFFIC = {(800, 800, 800): (259.325184e6 + 201.005312e6) * 8.0,
+                 (400, 400, 400): 259.325184e6 + 201.005312e6}
+DENSE_TRAFFIC_SOURCE = ("ncu --set full of k_dense_tma<5,0> at 400^3 (one launch), "
+                        "scaled by elements to the timed size")
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -44,6 +54,7 @@ def parse():
     ap.add_argument("--upsilon", type=float, default=3.0)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the per-form comparison")
     return ap.parse_args()
 
 
@@ -252,9 +263,52 @@ def run_ours(a, rank, world):
         peak, src = peaks()
         achieved = alg_bytes / (dms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "k_dense_fp32",
+                "frac": achieved / peak, "traffic": DENSE_TRAFFIC.get(tuple(p.dims)) if p.ranks[-1] == 5 else None,
+                "traffic_source": DENSE_TRAFFIC_SOURCE if tuple(p.dims) in DENSE_TRAFFIC else None,
+                "kernel": f"k_dense_tma<{p.ranks[-1]},0>",
                 "ms_per_launch": dms, "peak_source": f"{src} (burst copy bandwidth)",
                 "algorithmic_bytes_per_launch": alg_bytes}
+    # --- dense-pass forms: same iterates, different evaluation of L in the dense pass ---
+    forms_out = None
+    if scope == rt.SCOPE_FULL and not a.no_forms:
+        forms_out = {}
+        S_ref = S.clone()
+        rt.rtcur_threshold_dense(plan, 1, sh)  # FP32 form at the plan's current state
+        torch.cuda.synchronize()
+        S_ref.copy_(S)
+        for name, form in (("fp32_plain", rt.FORM_FP32_PLAIN), ("bf16", rt.FORM_BF16),
+                           ("tf32", rt.FORM_TF32)):
+            try:
+                fp = rt.rtcur_create(p.dims, p.ranks, p.m, p.q, p.zeta0, p.gamma, p.tol, max_iter,
+                                     variant, rt.make_options(scope=scope, dense_form=form))
+            except rt.RTCURError as exc:
+                forms_out[name] = {"unavailable": str(exc)}
+                continue
+            Sf = torch.empty_like(X)
+            rt.rtcur_begin(fp, X.data_ptr(), idx, Sf.data_ptr(), sh)
+            rt.rtcur_iterate(fp, W, sh)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            rt.rtcur_iterate(fp, K, sh)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            fms = ev0.elapsed_time(ev1)
+            rt.rtcur_threshold_dense(fp, 2, sh)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            rt.rtcur_threshold_dense(fp, 5, sh)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            dms_f = ev0.elapsed_time(ev1) / 5
+            mism = int(((Sf != 0) != (S_ref != 0)).sum().item())
+            rt.rtcur_destroy(fp)
+            forms_out[name] = {"iters_per_s": K / (fms / 1e3), "ms_per_iter": fms / K,
+                               "dense_ms": dms_f,
+                               "dense_gbs": 8.0 * float(np.prod(p.dims)) / (dms_f / 1e3) / 1e9,
+                               "S_support_mismatch_vs_fp32": mism,
+                               "note": "same CUR iterates as the FP32 form; only S differs, near the threshold"}
+        forms_out["fp32_fused"] = {"iters_per_s": value / world, "ms_per_iter": ms / K,
+                                   "dense_ms": roof["ms_per_launch"] if roof else None}
     # --- time to tolerance: whole solve from X resident, one graph launch ---
     ev0.record(stream)
     res = rt.rtcur_solve(plan, X.data_ptr(), idx, L.data_ptr(), S.data_ptr(), sh, max_iter=max_iter)
@@ -294,6 +348,7 @@ def run_ours(a, rank, world):
                 "h2d_bytes_per_step": int(p.X.nbytes), "d2h_bytes_per_step": int(p.X.nbytes),
                 "step": "one whole solve: H2D X, rtcur_solve to 1e-5, D2H L"},
         "roofline": roof,
+        "forms": forms_out,
         "gpu_launches": launches_per_iter * K,
         "clocks": clk.summary(),
     }
