@@ -438,7 +438,10 @@ __device__ void twisted_vector(const float* d, const float* e, int m, float lam,
 __global__ void __launch_bounds__(kJacThreads, 1) k_eig_tri(Geom g, Bufs b) {
   TL_BEGIN();
   extern __shared__ float smem[];
-  if (b.warm[blockIdx.x]) return;  // warm attempt certified for this mode
+  if (b.warm[blockIdx.x]) {  // warm attempt certified for this mode
+    TL_END(16);
+    return;
+  }
   __shared__ float dv[kTriMax], ev[kTriMax], e2[kTriMax], tauv[kTriMax], vb[kTriMax], pv[kTriMax];
   __shared__ float lam[kTriMax], qt[kTriMax];
   __shared__ int cid[kTriMax], inbig[kTriMax], known[kTriMax];
@@ -756,6 +759,29 @@ __device__ void cluster_barrier() {
 // and E (re-read from global memory after each cluster barrier), the FP32 basis restricted to
 // this CTA's columns and rows, and a chunk of W columns for Y = W^T Q_r Sigma^-2.
 constexpr int kWChunk = 32;
+constexpr int kWarmMaxSteps = 12;  // subspace-iteration steps a warm attempt may take
+
+// In-place Cholesky of the r x r SPD matrix G (row-major; the lower triangle is read and
+// overwritten with L, G = L L^T); inv[j] = 1 / L_jj so triangular solves multiply instead of
+// divide (FP64 division is a long dependent sequence on this part). Returns false when a pivot
+// is not positive. One thread.
+__device__ bool chol_small(double* G, int r, double* inv) {
+  for (int j = 0; j < r; ++j) {
+    double d = G[j * r + j];
+    for (int l = 0; l < j; ++l) d -= G[j * r + l] * G[j * r + l];
+    if (!(d > 0.0)) return false;
+    d = sqrt(d);
+    const double id = 1.0 / d;
+    G[j * r + j] = d;
+    inv[j] = id;
+    for (int ii = j + 1; ii < r; ++ii) {
+      double v = G[ii * r + j];
+      for (int l = 0; l < j; ++l) v -= G[ii * r + l] * G[j * r + l];
+      G[ii * r + j] = v * id;
+    }
+  }
+  return true;
+}
 
 __host__ __device__ inline size_t refine_smem_bytes(int m, int r, int ncl) {
   int own = (m + ncl - 1) / ncl;
@@ -802,6 +828,7 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
   __shared__ double Hs[RT_MAXR * RT_MAXR];
   __shared__ double Yh[RT_MAXR * RT_MAXR];
   __shared__ double wv[RT_MAXR];
+  __shared__ double invd[RT_MAXR];
   __shared__ int order[RT_MAXR];
   __shared__ int tie;
   __shared__ float lam[RT_MAXM];
@@ -829,8 +856,13 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
   float* sW = sXr + (size_t)ownmax * m;      // m x kWChunk
 
   long long tph = clock64();
+  int wsteps = 3, wtotal = 0;  // warm attempt: steps of the next round, steps taken so far
+  __shared__ int warm_retry;
   int* warm_flag = b.warm + i;
-  if (mode == 1 && *warm_flag) return;  // the warm attempt already produced this mode's factors
+  if (mode == 1 && *warm_flag) {  // the warm attempt already produced this mode's factors
+    TL_END(15);
+    return;
+  }
   if (mode == 0) {
     if (tid == 0 && crank == 0) *warm_flag = 0;
     if (g.variant != 0 || b.st->k < 1) return;
@@ -867,7 +899,8 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
     load_panel(sX1, X1, m * r);
     __syncthreads();
     __shared__ int chol_ok;
-    for (int it = 0; it < 3; ++it) {
+  warm_steps:
+    for (int it = 0; it < wsteps; ++it) {
       for (int t0 = tid >> 2; t0 < ((own * r + nq - 1) / nq) * nq; t0 += nq) {
         const int t = t0;
         const bool act = t < own * r;
@@ -891,21 +924,7 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
         if (lane == 0) Gq[t] = acc;
       }
       __syncthreads();
-      if (tid == 0) {
-        chol_ok = 1;
-        for (int j = 0; j < r && chol_ok; ++j) {
-          double d = Gq[j * r + j];
-          for (int l = 0; l < j; ++l) d -= Gq[j * r + l] * Gq[j * r + l];
-          if (!(d > 0.0)) { chol_ok = 0; break; }
-          d = sqrt(d);
-          Gq[j * r + j] = d;
-          for (int ii = j + 1; ii < r; ++ii) {
-            double v = Gq[ii * r + j];
-            for (int l = 0; l < j; ++l) v -= Gq[ii * r + l] * Gq[j * r + l];
-            Gq[ii * r + j] = v / d;
-          }
-        }
-      }
+      if (tid == 0) chol_ok = chol_small(Gq, r, invd) ? 1 : 0;
       __syncthreads();
       if (!chol_ok) return;  // uniform across the cluster (same data): the full path runs
       for (int a = lo + tid; a < hi; a += blockDim.x) {
@@ -915,7 +934,7 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
           if (j < r) {
             double v = sYw[a * r + j];
             for (int l = 0; l < j; ++l) v -= Gq[j * r + l] * y[l];
-            y[j] = v / Gq[j * r + j];
+            y[j] = v * invd[j];
           }
         }
 #pragma unroll
@@ -926,6 +945,7 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
       load_panel(sX1, X1, m * r);
       __syncthreads();
     }
+    wtotal += wsteps;
   } else {
   for (int t = tid; t < own * r; t += blockDim.x) {
     int a = lo + t / r, j = t % r;
@@ -1064,39 +1084,46 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
   }
   __syncthreads();
   __shared__ int fast_ok;
-  __shared__ double cert[2];
+  __shared__ double cert[3];
   if (mode == 0) {
-    // certificate, summed over the cluster: trace(M) and ||M X - X H||_F^2 (own rows)
-    double trp = 0.0, rsp = 0.0;
-    for (int a = tid; a < own; a += blockDim.x) trp += sM[(size_t)a * m + lo + a];
+    // certificate, summed over the cluster (own rows): ||M||_F^2, ||R||_F^2 with
+    // R = M X - X H, and ||M X||_F^2
+    double fmp = 0.0, rsp = 0.0, mxp = 0.0;
+    for (int t = tid; t < own * m; t += blockDim.x) fmp = fma(sM[t], sM[t], fmp);
     for (int t = tid; t < own * r; t += blockDim.x) {
       int a = t / r, j = t - a * r;
-      double v = sYw[(lo + a) * r + j];
+      double mx = sYw[(lo + a) * r + j];
+      double v = mx;
       for (int l = 0; l < r; ++l) v -= sX1[(lo + a) * r + l] * Hs[l * r + j];
       rsp = fma(v, v, rsp);
+      mxp = fma(mx, mx, mxp);
     }
-    trp = warp_sum_d(trp);
+    fmp = warp_sum_d(fmp);
     rsp = warp_sum_d(rsp);
-    __shared__ double wpart[2][32];
-    if (lane == 0) { wpart[0][wid] = trp; wpart[1][wid] = rsp; }
+    mxp = warp_sum_d(mxp);
+    __shared__ double wpart[3][32];
+    if (lane == 0) { wpart[0][wid] = fmp; wpart[1][wid] = rsp; wpart[2][wid] = mxp; }
     __syncthreads();
     if (tid == 0) {
-      double a0 = 0.0, a1 = 0.0;
-      for (int w = 0; w < nw; ++w) { a0 += wpart[0][w]; a1 += wpart[1][w]; }
-      double* slot = b.ework + 3 * g.sumMR + (long long)(i * NCL + crank) * 2;
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+      for (int w = 0; w < nw; ++w) { a0 += wpart[0][w]; a1 += wpart[1][w]; a2 += wpart[2][w]; }
+      double* slot = b.ework + 3 * g.sumMR + (long long)(i * NCL + crank) * 3;
       slot[0] = a0;
       slot[1] = a1;
+      slot[2] = a2;
     }
     cluster_barrier();
     if (tid == 0) {
-      double a0 = 0.0, a1 = 0.0;
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0;
       for (int c2 = 0; c2 < NCL; ++c2) {
-        const double* slot = b.ework + 3 * g.sumMR + (long long)(i * NCL + c2) * 2;
+        const double* slot = b.ework + 3 * g.sumMR + (long long)(i * NCL + c2) * 3;
         a0 += slot[0];
         a1 += slot[1];
+        a2 += slot[2];
       }
       cert[0] = a0;
       cert[1] = a1;
+      cert[2] = a2;
     }
     __syncthreads();
   }
@@ -1133,15 +1160,21 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
     float lmx = 0.f, lmn = 3.4e38f;
     for (int j = 0; j < r; ++j) { lmx = fmaxf(lmx, hf[j * r + j]); lmn = fminf(lmn, hf[j * r + j]); }
     fast_ok = (lmx > 0.f && lmn > 1e-6f * lmx) ? 1 : 0;
+    warm_retry = 0;
     if (mode == 0 && fast_ok) {
-      // M is PSD, so trace(M) - trace(H) bounds the sum of the eigenvalues outside span(X).
-      // If that is below lambda_min(H) / 2, span(X) is the top-r invariant subspace with a gap of
-      // at least lambda_min(H) / 2, and the residual bounds its error by 2 ||R|| / lambda_min(H).
-      double trH = 0.0;
-      for (int j = 0; j < r; ++j) trH += Hs[j * r + j];
-      const double tail = cert[0] - trH;
+      // In the basis [X, X_perp] (X orthonormal), M = [[H, B^T], [B, C]] with ||B||_F = ||R||_F
+      // and ||C||_F^2 = ||M||_F^2 - ||M X||_F^2 - ||R||_F^2. ||C||_F bounds the largest eigenvalue
+      // outside span(X). If it is below lambda_min(H) / 2 and ||R|| is tiny, Weyl's inequality
+      // separates the top r eigenvalues of M from the rest by about lambda_min(H) / 2 and the
+      // sin-theta theorem bounds the error of span(X) by ~2 ||R|| / lambda_min(H).
+      const double c2 = cert[0] - cert[2] - cert[1];
       const double lmin = (double)lmn;
-      if (!(tail < 0.5 * lmin && sqrt(fmax(cert[1], 0.0)) <= 1e-11 * lmin)) fast_ok = 0;
+      const bool tail_ok = sqrt(fmax(c2, 0.0)) < 0.5 * lmin;
+      const bool res_ok = sqrt(fmax(cert[1], 0.0)) <= 1e-11 * lmin;
+      if (!(tail_ok && res_ok)) fast_ok = 0;
+      // separated but not yet converged: more subspace steps (each shrinks the error by the
+      // ratio lambda_{r+1} / lambda_r, about 1/2 or less once the tail test passes)
+      if (tail_ok && !res_ok && wtotal + 2 <= kWarmMaxSteps) warm_retry = 1;
     }
     if (fast_ok) {
       // singular values (diagnostic), descending
@@ -1151,23 +1184,16 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
           if (wv[l] > wv[j]) { double t = wv[j]; wv[j] = wv[l]; wv[l] = t; }
       // FP64 Cholesky H = L L^T into Gq
       for (int t = 0; t < r * r; ++t) Gq[t] = 0.5 * (Hs[t] + Hs[(t % r) * r + t / r]);
-      for (int j = 0; j < r; ++j) {
-        double d = Gq[j * r + j];
-        for (int l = 0; l < j; ++l) d -= Gq[j * r + l] * Gq[j * r + l];
-        if (!(d > 0.0)) { fast_ok = 0; break; }
-        d = sqrt(d);
-        Gq[j * r + j] = d;
-        for (int ii = j + 1; ii < r; ++ii) {
-          double v = Gq[ii * r + j];
-          for (int l = 0; l < j; ++l) v -= Gq[ii * r + l] * Gq[j * r + l];
-          Gq[ii * r + j] = v / d;
-        }
-      }
+      if (!chol_small(Gq, r, invd)) fast_ok = 0;
     }
     if (tie && crank == 0) atomicOr(&b.st->flags, 2);
     else if (tie) atomicOr(&b.st->flags, 2);
   }
   __syncthreads();
+  if (mode == 0 && warm_retry) {  // uniform: every CTA of the cluster sums the same slots
+    wsteps = 2;
+    goto warm_steps;
+  }
   if (fast_ok) {
     // P = X1 H^-1 on own rows (solve L L^T p = x1_a), Qr = X1
     for (int a = lo + tid; a < hi; a += blockDim.x) {
@@ -1177,7 +1203,7 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
         if (j < r) {
           double v = sX1[a * r + j];
           for (int l = 0; l < j; ++l) v -= Gq[j * r + l] * y[l];
-          y[j] = v / Gq[j * r + j];
+          y[j] = v * invd[j];
         }
       }
 #pragma unroll
@@ -1185,7 +1211,7 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
         if (j < r) {
           double v = y[j];
           for (int l = j + 1; l < r; ++l) v -= Gq[l * r + j] * y[l];
-          y[j] = v / Gq[j * r + j];
+          y[j] = v * invd[j];
         }
       }
 #pragma unroll
@@ -1225,6 +1251,7 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
       atomicAdd((unsigned long long*)&b.st->warm_hits, 1ull);
     }
     PHASE_MARK(tph, "ref.fast");
+    TL_END(4 + 10 * mode);
     return;
   }
   if (mode == 0) return;  // not certified: the eigensolver and the full refinement run

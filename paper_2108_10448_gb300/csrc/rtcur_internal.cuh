@@ -120,7 +120,7 @@ struct Bufs {
   double* Qr;            // sum m_i r_i, final orthonormal top-r basis
   double* sig;           // sum r_i, singular values (0 where truncated)
   double* Y;             // sum q_i r_i, V_r Sigma_r^-1
-  double* ework;         // 3 * sum m_i r_i + 2 * 16 * n, refinement scratch
+  double* ework;         // 3 * sum m_i r_i + 3 * 16 * n, refinement scratch
   int* warm;             // n flags: the warm attempt produced mode i's factors this iteration
   double* Bpart;         // split-K partials of B (nchunk * sumB)
   float* B[2];           // sumB each
