@@ -322,6 +322,7 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
   AL(b.Y, oY);
   AL(b.ework, 3 * oQ + 3 * 16 * RT_MAXN);
   AL(b.warm, RT_MAXN);
+  AL(b.wratio, RT_MAXN);
   AL(b.Bpart, g.nchunk * g.sumB);
   AL(b.B[0], g.sumB);
   AL(b.B[1], g.sumB);
@@ -408,6 +409,7 @@ rtcur_status rtcur_begin(rtcur_plan* p, const float* X, const int64_t* idx, floa
   CKC(p, cudaMemsetAsync(b.B[0], 0, sizeof(float) * g.sumB, s));
   CKC(p, cudaMemsetAsync(b.G[0], 0, sizeof(float) * g.nG, s));
   CKC(p, cudaMemsetAsync(b.warm, 0, sizeof(int) * RT_MAXN, s));
+  CKC(p, cudaMemsetAsync(b.wratio, 0, sizeof(double) * RT_MAXN, s));
   if (b.Ap[0]) {
     CKC(p, cudaMemsetAsync(b.Ap[0], 0, sizeof(float) * g.sumDM, s));
     CKC(p, cudaMemsetAsync(b.Rp[0], 0, sizeof(float) * g.nR, s));

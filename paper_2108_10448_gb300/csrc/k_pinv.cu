@@ -760,6 +760,7 @@ __device__ void cluster_barrier() {
 // this CTA's columns and rows, and a chunk of W columns for Y = W^T Q_r Sigma^-2.
 constexpr int kWChunk = 32;
 constexpr int kWarmMaxSteps = 12;  // subspace-iteration steps a warm attempt may take
+constexpr double kWarmGate = 1.5;  // attempt only if ||C||_F / lambda_r was below this last time
 
 // In-place Cholesky of the r x r SPD matrix G (row-major; the lower triangle is read and
 // overwritten with L, G = L L^T); inv[j] = 1 / L_jj so triangular solves multiply instead of
@@ -866,6 +867,9 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
   if (mode == 0) {
     if (tid == 0 && crank == 0) *warm_flag = 0;
     if (g.variant != 0 || b.st->k < 1) return;
+    // skip the attempt when the last iteration's spectrum had no usable gap: its complement
+    // block was at least kWarmGate times lambda_r, and the block moves slowly between iterations
+    if (b.wratio[i] > kWarmGate) return;
   }
   if (tid == 0) {
     tie = 0;
@@ -876,6 +880,13 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
         if (pos_of[a] < 0 && (best < 0 || lam[a] > lam[best])) best = a;
       top[j] = best;
       pos_of[best] = j;
+    }
+    if (mode == 1 && crank == 0) {  // the gate for the next warm attempt, from this spectrum
+      double t2 = 0.0;
+      for (int a = 0; a < m; ++a)
+        if (pos_of[a] < 0) t2 += (double)lam[a] * (double)lam[a];
+      const double lr = (double)lam[top[r - 1]];
+      b.wratio[i] = (lr > 0.0) ? sqrt(t2) / lr : 1e30;
     }
   }
   for (int t = tid; t < own * m; t += blockDim.x) {
@@ -1172,6 +1183,7 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
       const bool tail_ok = sqrt(fmax(c2, 0.0)) < 0.5 * lmin;
       const bool res_ok = sqrt(fmax(cert[1], 0.0)) <= 1e-11 * lmin;
       if (!(tail_ok && res_ok)) fast_ok = 0;
+      if (crank == 0) b.wratio[i] = sqrt(fmax(c2, 0.0)) / lmin;
       // separated but not yet converged: more subspace steps (each shrinks the error by the
       // ratio lambda_{r+1} / lambda_r, about 1/2 or less once the tail test passes)
       if (tail_ok && !res_ok && wtotal + 2 <= kWarmMaxSteps) warm_retry = 1;

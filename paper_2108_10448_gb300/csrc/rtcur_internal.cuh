@@ -122,6 +122,7 @@ struct Bufs {
   double* Y;             // sum q_i r_i, V_r Sigma_r^-1
   double* ework;         // 3 * sum m_i r_i + 3 * 16 * n, refinement scratch
   int* warm;             // n flags: the warm attempt produced mode i's factors this iteration
+  double* wratio;        // n: ||C||_F / lambda_r of the last iteration (warm-attempt gate)
   double* Bpart;         // split-K partials of B (nchunk * sumB)
   float* B[2];           // sumB each
   float* G[2];           // nG each
