@@ -77,7 +77,11 @@ typedef struct rtcur_options {
   double inband_rel;         /* half-width of the reported threshold band, relative to zeta; 1e-6 */
   int32_t eig_method;        /* FP32 eigenbasis of the pinv: 0 tridiagonal + inverse iteration
                                 (used when every |I_i| <= 128, default), 1 cyclic Jacobi */
-  int32_t reserved[7];       /* must be zero */
+  int32_t checkpoint;        /* record the first `checkpoint` iterations for rtcur_backward
+                                (their sampled values X - S and HT masks, 5 B per sampled entry
+                                per iteration); 0 = off (default). Requires n_modes == 3 and
+                                checkpoint <= max_iter. */
+  int32_t reserved[6];       /* must be zero */
 } rtcur_options;
 
 typedef struct rtcur_result {
@@ -181,6 +185,21 @@ RTCUR_API rtcur_status rtcur_get_factors(rtcur_plan* plan, float* G, float* B, i
                                void* stream);
 
 /* Sizes of the plan's sampled-entry buffer and of its segments, for callers that read it. */
+/* Adjoint of the last solve (Algorithm 1 unrolled over its K iterations, K = the iteration count
+ * of the last rtcur_solve / rtcur_finish): dX = (dL^(K)/dX)^T dL, the vector-Jacobian product of
+ * X -> L^(K) = R x_i (C_i U_i^+) (Eq. (L=CUR)) with dL (device, FP32, dims, row-major).
+ * Hard thresholding (Eq. (HT)) is differentiated almost everywhere, with each iteration's support
+ * masks on the sampled entries frozen at their forward values: an unmasked sampled entry passes
+ * its adjoint to X, a masked one to the previous L^(k). The truncated pseudoinverse U_i^+ is
+ * differentiated where sigma_{r_i} > sigma_{r_i+1} > ... (a.e.), through the eigenpairs of
+ * U_i U_i^T (FP64 Jacobi, Daleckii-Krein divided differences). Only L^(K) depends on X through
+ * the sampled entries, so dX is zero off the sample.
+ * dX: device, FP32, dims, overwritten (16-byte aligned). dL may alias nothing the plan owns.
+ * Requires a plan created with options.checkpoint >= K (and n_modes == 3); otherwise
+ * RTCUR_EINVAL. Synchronises the stream once (to read K). Uses plan-owned workspace sized at
+ * create; allocates nothing. */
+RTCUR_API rtcur_status rtcur_backward(rtcur_plan* plan, const float* dL, float* dX, void* stream);
+
 RTCUR_API int64_t rtcur_sample_count(const rtcur_plan* plan);
 
 /* Last error message of a plan (NULL plan: the last create failure); never NULL. */

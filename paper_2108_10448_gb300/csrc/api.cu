@@ -9,6 +9,7 @@
 // They join before the commit kernel, which advances k and zeta and sets the loop condition.
 // rtcur_solve launches a graph whose single node is a conditional WHILE over that body, so the
 // whole solve runs on the device with one host synchronisation at the end.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -31,6 +32,7 @@ struct rtcur_plan {
   cudaEvent_t evFork = nullptr, evJoin = nullptr;
   cudaGraph_t loopG = nullptr, iterG = nullptr;
   cudaGraphExec_t loopX = nullptr, iterX = nullptr;
+  BwWork bw;             // adjoint workspace (options.checkpoint > 0)
   std::vector<void*> allocs;
   std::vector<int> pos_host;
   std::string err;
@@ -176,7 +178,7 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
   o.inband_rel = 1e-6;
   if (opt) {
     o = *opt;
-    for (int i = 0; i < 7; ++i)
+    for (int i = 0; i < 6; ++i)
       if (o.reserved[i] != 0) return fail(nullptr, RTCUR_EINVAL, "options.reserved must be zero");
     if (o.refine_steps == 0 && o.jacobi_max_sweeps == 0 && o.inband_rel == 0.0) {
       o.refine_steps = 2; o.jacobi_max_sweeps = 30; o.inband_rel = 1e-6;
@@ -188,6 +190,8 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
   if (o.jacobi_max_sweeps < 1 || o.jacobi_max_sweeps > 100) return fail(nullptr, RTCUR_EINVAL, "jacobi_max_sweeps must be in [1, 100]");
   if (!(o.inband_rel >= 0.0 && o.inband_rel < 1.0)) return fail(nullptr, RTCUR_EINVAL, "inband_rel must be in [0, 1)");
   if (o.eig_method != 0 && o.eig_method != 1) return fail(nullptr, RTCUR_EINVAL, "eig_method must be 0 (tridiagonal) or 1 (Jacobi)");
+  if (o.checkpoint < 0 || o.checkpoint > max_iter) return fail(nullptr, RTCUR_EINVAL, "checkpoint must be in [0, max_iter]");
+  if (o.checkpoint > 0 && n_modes != 3) return fail(nullptr, RTCUR_EINVAL, "checkpoint (the adjoint) needs n_modes == 3");
 
   Geom g;
   memset(&g, 0, sizeof g);
@@ -222,6 +226,7 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
   g.gamma = gamma;
   g.tol = tol;
   g.inband = o.inband_rel;
+  g.ck_iters = o.checkpoint;
   g.nR = 1;
   g.nG = 1;
   for (int i = 0; i < n_modes; ++i) {
@@ -290,6 +295,8 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   int mx = 0;
   for (int i = 0; i < n_modes; ++i) mx = g.m[i] > mx ? g.m[i] : mx;
+  if (o.checkpoint > 0 && mx > 160)
+    return fail(nullptr, RTCUR_EINVAL, "checkpoint (the adjoint) needs every |I_i| <= 160");
   if (jacobi_smem_bytes(mx) > (size_t)optin)
     return fail(nullptr, RTCUR_EINVAL, "|I_i| = %d needs %zu bytes of shared memory (device allows %d)", mx, jacobi_smem_bytes(mx), optin);
 
@@ -351,6 +358,40 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
     AL(b.Z1p, (long long)g.m[0] * g.m[1] * g.d[2]);
     AL(b.Z2p, (long long)g.m[0] * g.d[1] * g.d[2]);
     AL(b.Lplain, g.N);
+  }
+  if (o.checkpoint > 0) {
+    AL(b.ckV, (long long)o.checkpoint * g.nS);
+    AL(b.ckM, (long long)o.checkpoint * g.nS);
+    BwWork& w = p->bw;
+    memset(&w, 0, sizeof w);
+    backward_layout(g, w);
+    const long long K = o.checkpoint;
+    long long mq = 0, mm = 0;
+    for (int i = 0; i < n_modes; ++i) {
+      mq = std::max(mq, (long long)g.m[i] * g.q[i]);
+      mm = std::max(mm, (long long)g.m[i] * g.m[i]);
+    }
+    AL(w.W, K * w.slotW);
+    AL(w.U, K * w.slotMM);
+    AL(w.lam, K * w.slotM);
+    AL(w.Z, K * w.slotMM);
+    AL(w.P, K * w.slotQM);
+    AL(w.A, K * w.slotDM);
+    AL(w.Vb, g.nS);
+    AL(w.Lb, g.nS);
+    AL(w.Ab, w.slotDM);
+    AL(w.Pb, mq);
+    AL(w.Wb, mq);
+    AL(w.T0, mm);
+    AL(w.T1, mm);
+    AL(w.Pi, w.slotMM);
+    AL(w.Zf, mq);
+    AL(w.Zfb, mq);
+    AL(w.tmp0, w.tmpsz);
+    AL(w.tmp1, w.tmpsz);
+    AL(w.dX64, g.N);
+    AL(w.part, w.partsz);
+    if (e == cudaSuccess) e = prepare_backward(mx);
   }
 #undef AL
   // the latency-bound sampled chain is captured from a high-priority stream, the bandwidth-bound
@@ -503,6 +544,25 @@ rtcur_status rtcur_get_factors(rtcur_plan* p, float* G, float* B, int32_t* k, do
   if (B) CKC(p, cudaMemcpy(B, p->b.B[cp], sizeof(float) * p->g.sumB, cudaMemcpyDeviceToHost));
   if (k) *k = h.k;
   if (zeta) *zeta = h.zeta;
+  return RTCUR_OK;
+}
+
+rtcur_status rtcur_backward(rtcur_plan* p, const float* dL, float* dX, void* stream) {
+  if (!p) return fail(nullptr, RTCUR_EINVAL, "plan is NULL");
+  if (!dL || !dX) return fail(p, RTCUR_EINVAL, "dL and dX must not be NULL");
+  if (!aligned16(dX)) return fail(p, RTCUR_EINVAL, "dX must be 16-byte aligned");
+  const Geom& g = p->g;
+  if (g.ck_iters <= 0) return fail(p, RTCUR_EINVAL, "the plan records no iterations (options.checkpoint = 0)");
+  if (!p->begun) return fail(p, RTCUR_EINVAL, "no solve to differentiate");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  State h;
+  CKC(p, cudaMemcpyAsync(&h, p->b.st, sizeof h, cudaMemcpyDeviceToHost, s));
+  CKC(p, cudaStreamSynchronize(s));
+  if (h.k < 1) return fail(p, RTCUR_EINVAL, "the solve ran no iteration");
+  if (h.k > g.ck_iters)
+    return fail(p, RTCUR_EINVAL, "the solve ran %d iterations, more than the %d recorded", h.k, g.ck_iters);
+  if (h.err != 0) return fail(p, (rtcur_status)h.err, "the forward pass latched device error %d", h.err);
+  CKC(p, launch_backward(g, p->b, p->bw, h.k, dL, dX, s));
   return RTCUR_OK;
 }
 

@@ -161,6 +161,10 @@ __global__ void __launch_bounds__(kThreads) k_sample_ht(Geom g, Bufs b) {
     bool keep = ad > zf;                 // HT_zeta keeps |x| > zeta (strict)
     const float xs = keep ? L : x;       // (X - S) = X - (X - L) = L where S is nonzero
     b.XS[e] = xs;
+    if (k < g.ck_iters) {                // checkpoint for the adjoint
+      b.ckV[(long long)k * g.nS + e] = xs;
+      b.ckM[(long long)k * g.nS + e] = keep ? 1 : 0;
+    }
     if (seg > 0) {                       // fiber entry: also W_i = C_i(I_i, :) when t is in I_i
       const int i = seg - 1;
       const unsigned local = (unsigned)(e - g.seg[seg]);

@@ -40,6 +40,7 @@ struct Geom {
   int ncl;                       // CTAs per cluster in the FP64 refinement (16 or 8)
   int dense_ctas;                // persistent CTAs of the dense pass (0: default)
   int dense_form;                // RTCUR_FORM_* of the dense pass
+  int ck_iters;                  // iterations recorded for the adjoint (0: none)
   int nG;                       // prod r_i
   int rlast;                    // r_n
   long long d[RT_MAXN];
@@ -141,7 +142,31 @@ struct Bufs {
   float* Lplain;         // plain form: the materialised L^(k)
   TlRec* tl;             // diagnostic timeline (null unless built with -DRTCUR_TIMELINE)
   unsigned* tl_n;
+  float* ckV;            // ck_iters * nS: sampled values X - S of each recorded iteration
+  unsigned char* ckM;    // ck_iters * nS: their HT masks (1 = thresholded, the value is L^(k))
 };
+
+// Workspace of the adjoint (rtcur_backward), 3-mode tensors. Per recorded iteration and mode:
+// W_i (m x q), U (m x m; first M = W W^T, then its eigenvectors), lambda (m), Z (m x m),
+// P_i = U_i^+ (q x m) and A_i = C_i P_i (d x m), all FP64; then one set of adjoint buffers.
+struct BwWork {
+  double *W, *U, *lam, *Z, *P, *A;
+  long long offW[RT_MAXN], offMM[RT_MAXN], offM[RT_MAXN], offQM[RT_MAXN], offDM[RT_MAXN];
+  long long slotW, slotMM, slotM, slotQM, slotDM;
+  double* Vb;    // nS: slot adjoint (R segment = R_bar, fiber segments = C_bar_i)
+  double* Lb;    // nS: adjoint of L^(k) at the slots
+  double* Ab;    // slotDM: A_bar_i
+  double *Pb, *Wb, *T0, *T1, *Pi, *Zf, *Zfb;
+  double *tmp0, *tmp1;  // tmpsz each
+  double* dX64;  // N
+  double* part;  // partsz: split-K partial sums
+  long long tmpsz, partsz;
+};
+
+void backward_layout(const Geom& g, BwWork& w);
+cudaError_t prepare_backward(int max_m);
+cudaError_t launch_backward(const Geom& g, const Bufs& b, const BwWork& w, int K, const float* dL,
+                            float* dX, cudaStream_t s);
 
 enum { TK_SAMPLE = 0, TK_ERR = 1, TK_DENSE = 2, TK_MAXABS = 3, TK_COUNT = 8 };
 

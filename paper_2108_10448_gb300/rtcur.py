@@ -22,7 +22,7 @@ FLAG_RANK_DEFICIENT, FLAG_TIE = 1, 2
 class rtcur_options(C.Structure):
     _fields_ = [("scope", C.c_int32), ("dense_form", C.c_int32), ("refine_steps", C.c_int32),
                 ("jacobi_max_sweeps", C.c_int32), ("inband_rel", C.c_double),
-                ("eig_method", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("eig_method", C.c_int32), ("checkpoint", C.c_int32), ("reserved", C.c_int32 * 6)]
 
 
 class rtcur_result(C.Structure):
@@ -61,6 +61,7 @@ def load(path=LIB_PATH):
     lib.rtcur_iterate.argtypes = [P, C.c_int32, P]
     lib.rtcur_finish.argtypes = [P, P, P, C.POINTER(rtcur_result), P]
     lib.rtcur_threshold_dense.argtypes = [P, C.c_int32, P]
+    lib.rtcur_backward.argtypes = [P, P, P, P]
     lib.rtcur_threshold_dense_noalloc.argtypes = [C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
                                                   P, P, P, C.c_double, P, C.POINTER(C.c_double), P]
     lib.rtcur_threshold_dense_noalloc.restype = C.c_int
@@ -73,7 +74,7 @@ def load(path=LIB_PATH):
     lib.rtcur_destroy.argtypes = [P]
     lib.rtcur_destroy.restype = None
     for f in ("rtcur_create", "rtcur_solve", "rtcur_begin", "rtcur_iterate", "rtcur_finish",
-              "rtcur_get_factors", "rtcur_threshold_dense"):
+              "rtcur_get_factors", "rtcur_threshold_dense", "rtcur_backward"):
         getattr(lib, f).restype = C.c_int
     _lib = lib
     return lib
@@ -101,10 +102,11 @@ EIG_TRIDIAGONAL, EIG_JACOBI = 0, 1
 
 
 def make_options(scope=SCOPE_SAMPLED, dense_form=FORM_FP32, refine_steps=2, jacobi_max_sweeps=30,
-                 inband_rel=1e-6, eig_method=EIG_TRIDIAGONAL):
+                 inband_rel=1e-6, eig_method=EIG_TRIDIAGONAL, checkpoint=0):
     o = rtcur_options()
     o.scope, o.dense_form, o.refine_steps = scope, dense_form, refine_steps
     o.jacobi_max_sweeps, o.inband_rel, o.eig_method = jacobi_max_sweeps, inband_rel, eig_method
+    o.checkpoint = checkpoint
     return o
 
 
@@ -185,6 +187,12 @@ def rtcur_finish(plan, L_ptr=0, S_ptr=0, stream=0, max_iter=1000):
 
 def rtcur_threshold_dense(plan, n_launch=1, stream=0):
     _check(load().rtcur_threshold_dense(plan, int(n_launch), stream or None), plan)
+
+
+def rtcur_backward(plan, dL_ptr, dX_ptr, stream=0):
+    """dX = (dL^(K)/dX)^T dL for the last solve of a plan created with options.checkpoint >= K
+    (device pointers; masks of the thresholding frozen at their forward values)."""
+    _check(load().rtcur_backward(plan, dL_ptr, dX_ptr, stream or None), plan, allow=(OK,))
 
 
 def rtcur_threshold_dense_noalloc(dims, ranks, G_ptr, B_ptr, X_ptr, zeta, S_ptr, stream=0,

@@ -62,3 +62,15 @@ def test_options_reserved_must_be_zero(lib):
     with pytest.raises(rt.RTCURError) as ei:
         rt.rtcur_create([8, 8, 8], [2, 2, 2], [4, 4, 4], [8, 8, 8], 1.0, 0.7, 1e-5, 5, 0, o)
     assert ei.value.status == rt.EINVAL
+
+
+def test_checkpoint_options_are_validated(lib):
+    from paper_2108_10448_gb300 import rtcur as rt
+    for dims, ck, msg in (([8, 8, 8], 6, "checkpoint must be in"),
+                          ([8, 8, 8, 8], 2, "n_modes == 3")):
+        n = len(dims)
+        with pytest.raises(rt.RTCURError) as ei:
+            rt.rtcur_create(dims, [2] * n, [4] * n, [8] * n, 1.0, 0.7, 1e-5, 5, 0,
+                            rt.make_options(checkpoint=ck))
+        assert ei.value.status == rt.EINVAL
+        assert msg in str(ei.value)
