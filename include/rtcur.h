@@ -185,6 +185,22 @@ RTCUR_API rtcur_status rtcur_get_factors(rtcur_plan* plan, float* G, float* B, i
                                void* stream);
 
 /* Sizes of the plan's sampled-entry buffer and of its segments, for callers that read it. */
+/* Batched form: `count` independent problems (each with its own plan, so dims, ranks, sample
+ * sizes, variant and tolerance may all differ) solved together by ONE graph launch. The graph is
+ * a device-side WHILE loop whose body holds, per problem, a conditional IF node around that
+ * problem's Algorithm 1 iteration; a problem whose stopping test (Algorithm 1's loop condition)
+ * fails drops out, and the loop ends when none continues. No host synchronisation happens between
+ * iterations. X[i], idx[i], L_out[i], S_out[i] and res[i] are as for rtcur_solve on plans[i]
+ * (L_out, S_out, res may be NULL arrays; their entries may be NULL). Every plan must have
+ * tol < 1 and appear once. The graph is built on the first call for a given list of plans and
+ * cached with plans[0] (rebuilt when the list changes; destroying any listed plan invalidates
+ * it). Returns the first failing status of a problem, else RTCUR_OK (RTCUR_NOT_CONVERGED is
+ * reported per problem in res[i].status). */
+RTCUR_API rtcur_status rtcur_solve_batched(rtcur_plan* const* plans, int32_t count,
+                                           const float* const* X, const int64_t* const* idx,
+                                           float* const* L_out, float* const* S_out,
+                                           rtcur_result* res, void* stream);
+
 /* Adjoint of the last solve (Algorithm 1 unrolled over its K iterations, K = the iteration count
  * of the last rtcur_solve / rtcur_finish): dX = (dL^(K)/dX)^T dL, the vector-Jacobian product of
  * X -> L^(K) = R x_i (C_i U_i^+) (Eq. (L=CUR)) with dL (device, FP32, dims, row-major).

@@ -10,6 +10,7 @@
 // rtcur_solve launches a graph whose single node is a conditional WHILE over that body, so the
 // whole solve runs on the device with one host synchronisation at the end.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -20,7 +21,22 @@
 #include "../../include/rtcur.h"
 #include "rtcur_internal.cuh"
 
+struct rtcur_plan;
+
+// Cached graph of a batched solve (kept by the batch's first plan): a WHILE node whose body holds
+// one IF node per problem (the problem's iteration, skipped once it has stopped) and a kernel
+// that keeps the loop going while any problem continues.
+struct BatchGraph {
+  std::vector<rtcur_plan*> plans;
+  std::vector<unsigned long long> serials;
+  cudaGraph_t G = nullptr;
+  cudaGraphExec_t X = nullptr;
+  State** d_sts = nullptr;
+};
+
 struct rtcur_plan {
+  unsigned long long serial = 0;  // unique per plan (a batch cache is keyed by these)
+  BatchGraph* batch = nullptr;
   Geom g;
   Bufs b;
   rtcur_options opt;
@@ -42,6 +58,7 @@ struct rtcur_plan {
 namespace {
 
 thread_local std::string g_create_err = "no error";
+std::atomic<unsigned long long> g_serial{1};
 
 rtcur_status fail(rtcur_plan* p, rtcur_status st, const char* fmt, ...) {
   char buf[512];
@@ -126,6 +143,74 @@ rtcur_status build_graphs(rtcur_plan* p) {
   if (e != cudaSuccess) return fail(p, RTCUR_ECUDA, "capturing the loop body: %s", cudaGetErrorString(e));
   if (e2 != cudaSuccess) return fail(p, RTCUR_ECUDA, "ending body capture: %s", cudaGetErrorString(e2));
   CKC(p, cudaGraphInstantiate(&p->loopX, p->loopG, 0));
+  return RTCUR_OK;
+}
+
+void free_batch(BatchGraph* bg) {
+  if (!bg) return;
+  if (bg->X) cudaGraphExecDestroy(bg->X);
+  if (bg->G) cudaGraphDestroy(bg->G);
+  if (bg->d_sts) cudaFree(bg->d_sts);
+  delete bg;
+}
+
+rtcur_status build_batch(rtcur_plan* const* plans, int count, BatchGraph** out) {
+  rtcur_plan* p0 = plans[0];
+  BatchGraph* bg = new BatchGraph();
+  auto bail = [&](cudaError_t e, const char* what) {
+    free_batch(bg);
+    return fail(p0, RTCUR_ECUDA, "batched graph: %s: %s", what, cudaGetErrorString(e));
+  };
+  cudaError_t e;
+  std::vector<State*> sts(count);
+  for (int i = 0; i < count; ++i) {
+    bg->plans.push_back(plans[i]);
+    bg->serials.push_back(plans[i]->serial);
+    sts[i] = plans[i]->b.st;
+  }
+  if ((e = cudaMalloc(&bg->d_sts, sizeof(State*) * count)) != cudaSuccess) return bail(e, "cudaMalloc");
+  if ((e = cudaMemcpy(bg->d_sts, sts.data(), sizeof(State*) * count, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return bail(e, "cudaMemcpy");
+  if ((e = cudaGraphCreate(&bg->G, 0)) != cudaSuccess) return bail(e, "cudaGraphCreate");
+  cudaGraphConditionalHandle hw;
+  if ((e = cudaGraphConditionalHandleCreate(&hw, bg->G, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
+    return bail(e, "WHILE handle");
+  cudaGraphNodeParams wp = {cudaGraphNodeTypeConditional};
+  wp.conditional.handle = hw;
+  wp.conditional.type = cudaGraphCondTypeWhile;
+  wp.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  if ((e = cudaGraphAddNode(&wnode, bg->G, nullptr, nullptr, 0, &wp)) != cudaSuccess) return bail(e, "WHILE node");
+  cudaGraph_t body = wp.conditional.phGraph_out[0];
+  std::vector<cudaGraphNode_t> ifs(count);
+  for (int i = 0; i < count; ++i) {
+    rtcur_plan* p = plans[i];
+    cudaGraphConditionalHandle hp;
+    if ((e = cudaGraphConditionalHandleCreate(&hp, body, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
+      return bail(e, "IF handle");
+    cudaGraphNodeParams ip = {cudaGraphNodeTypeConditional};
+    ip.conditional.handle = hp;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    if ((e = cudaGraphAddNode(&ifs[i], body, nullptr, nullptr, 0, &ip)) != cudaSuccess) return bail(e, "IF node");
+    cudaGraph_t pb = ip.conditional.phGraph_out[0];
+    if ((e = cudaStreamBeginCaptureToGraph(p->cap, pb, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+      return bail(e, "capture begin");
+    cudaError_t ec = capture_body(p, p->cap, (unsigned long long)hp, 1);
+    cudaGraph_t tmp = nullptr;
+    e = cudaStreamEndCapture(p->cap, &tmp);
+    if (ec != cudaSuccess) return bail(ec, "capturing a problem's iteration");
+    if (e != cudaSuccess) return bail(e, "capture end");
+  }
+  if ((e = cudaStreamBeginCaptureToGraph(p0->cap, body, ifs.data(), nullptr, count, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+    return bail(e, "capture begin (join)");
+  cudaError_t ec = launch_batch_any(bg->d_sts, count, (unsigned long long)hw, p0->cap);
+  cudaGraph_t tmp = nullptr;
+  e = cudaStreamEndCapture(p0->cap, &tmp);
+  if (ec != cudaSuccess) return bail(ec, "join kernel");
+  if (e != cudaSuccess) return bail(e, "capture end (join)");
+  if ((e = cudaGraphInstantiate(&bg->X, bg->G, 0)) != cudaSuccess) return bail(e, "instantiate");
+  *out = bg;
   return RTCUR_OK;
 }
 
@@ -301,6 +386,7 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
     return fail(nullptr, RTCUR_EINVAL, "|I_i| = %d needs %zu bytes of shared memory (device allows %d)", mx, jacobi_smem_bytes(mx), optin);
 
   rtcur_plan* p = new rtcur_plan();
+  p->serial = g_serial.fetch_add(1);
   p->g = g;
   p->opt = o;
   p->zeta0 = zeta0;
@@ -522,6 +608,47 @@ rtcur_status rtcur_solve(rtcur_plan* p, const float* X, const int64_t* idx, floa
   return rtcur_finish(p, L_out, S_out, res, stream);
 }
 
+rtcur_status rtcur_solve_batched(rtcur_plan* const* plans, int32_t count, const float* const* X,
+                                 const int64_t* const* idx, float* const* L_out, float* const* S_out,
+                                 rtcur_result* res, void* stream) {
+  if (!plans || count < 1 || count > 4096) return fail(nullptr, RTCUR_EINVAL, "plans must hold 1..4096 plans");
+  if (!X || !idx) return fail(nullptr, RTCUR_EINVAL, "X and idx must not be NULL");
+  for (int i = 0; i < count; ++i) {
+    if (!plans[i]) return fail(nullptr, RTCUR_EINVAL, "plans[%d] is NULL", i);
+    if (!(plans[i]->g.tol < 1.0)) return fail(plans[i], RTCUR_EINVAL, "a batched problem needs tol < 1 (e^(0) = 1)");
+    for (int j = 0; j < i; ++j)
+      if (plans[j] == plans[i]) return fail(plans[i], RTCUR_EINVAL, "plans[%d] and plans[%d] are the same plan", j, i);
+  }
+  rtcur_plan* p0 = plans[0];
+  for (int i = 0; i < count; ++i) {
+    rtcur_plan* p = plans[i];
+    rtcur_status st = rtcur_begin(p, X[i], idx[i],
+                                  (p->g.scope == RTCUR_SCOPE_FULL && S_out) ? S_out[i] : nullptr, stream);
+    if (st != RTCUR_OK) return fail(p0, st, "problem %d: %s", i, p->err.c_str());
+  }
+  BatchGraph* bg = p0->batch;
+  bool hit = bg && (int)bg->plans.size() == count;
+  for (int i = 0; hit && i < count; ++i) hit = bg->plans[i] == plans[i] && bg->serials[i] == plans[i]->serial;
+  if (!hit) {
+    free_batch(bg);
+    p0->batch = nullptr;
+    rtcur_status st = build_batch(plans, count, &p0->batch);
+    if (st != RTCUR_OK) return st;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CKC(p0, cudaGraphLaunch(p0->batch->X, s));
+  rtcur_status worst = RTCUR_OK;
+  for (int i = 0; i < count; ++i) {
+    rtcur_status st = rtcur_finish(plans[i], L_out ? L_out[i] : nullptr, S_out ? S_out[i] : nullptr,
+                                   res ? &res[i] : nullptr, stream);
+    if (st != RTCUR_OK && worst == RTCUR_OK) {
+      worst = st;
+      if (i > 0) fail(p0, st, "problem %d: %s", i, plans[i]->err.c_str());
+    }
+  }
+  return worst;
+}
+
 rtcur_status rtcur_threshold_dense(rtcur_plan* p, int32_t n_launch, void* stream) {
   if (!p) return fail(nullptr, RTCUR_EINVAL, "plan is NULL");
   if (!p->begun) return fail(p, RTCUR_EINVAL, "rtcur_begin must come first");
@@ -589,6 +716,7 @@ const char* rtcur_last_error(const rtcur_plan* p) { return p ? p->err.c_str() : 
 void rtcur_destroy(rtcur_plan* p) {
   if (!p) return;
   cudaDeviceSynchronize();
+  free_batch(p->batch);
   if (p->loopX) cudaGraphExecDestroy(p->loopX);
   if (p->iterX) cudaGraphExecDestroy(p->iterX);
   if (p->loopG) cudaGraphDestroy(p->loopG);

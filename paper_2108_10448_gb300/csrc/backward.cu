@@ -458,8 +458,7 @@ size_t backward_eig_smem(int m) {
 
 cudaError_t prepare_backward(int max_m) {
   if (max_m > kEigMax) return cudaErrorInvalidValue;
-  return cudaFuncSetAttribute(k_bw_eig, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)backward_eig_smem(max_m));
+  return raise_smem_limit((const void*)k_bw_eig, (size_t)(backward_eig_smem(max_m)));
 }
 
 void backward_layout(const Geom& g, BwWork& w) {

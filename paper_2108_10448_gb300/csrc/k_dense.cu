@@ -395,7 +395,7 @@ cudaError_t prepare_tma_rn(size_t smem) {
   cudaError_t e = cudaSuccess;
   void* fns[3] = {(void*)k_dense_tma<RN, 0>, (void*)k_dense_tma<RN, 1>, (void*)k_dense_tma<RN, 2>};
   for (void* f : fns) {
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = raise_smem_limit((const void*)f, (size_t)(smem));
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   }
@@ -658,7 +658,7 @@ size_t mma_smem(const Geom& g, bool tf32) {
 template <int RN, bool TF>
 cudaError_t mma_launch_rn(const Geom& g, const Bufs& b, size_t smem, cudaStream_t s, bool prepare) {
   if (prepare) {
-    cudaError_t e = cudaFuncSetAttribute(k_dense_mma<RN, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem_limit((const void*)k_dense_mma<RN, TF>, smem);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_dense_mma<RN, TF>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                cudaSharedmemCarveoutMaxShared);

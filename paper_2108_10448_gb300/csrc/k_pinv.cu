@@ -1462,11 +1462,11 @@ constexpr size_t kFullSmem = sizeof(float) * 3 * kFullMaxN * kFullLd;
 constexpr size_t kTriSmem = sizeof(float) * 3 * kTriMax * kTriLd;
 
 cudaError_t prepare_jacobi(size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = raise_smem_limit((const void*)k_jacobi, (size_t)(smem));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_eig_tri, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTriSmem);
+  e = raise_smem_limit((const void*)k_eig_tri, (size_t)(kTriSmem));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_jacobi_full, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFullSmem);
+  return raise_smem_limit((const void*)k_jacobi_full, (size_t)(kFullSmem));
 }
 
 cudaError_t launch_jacobi(const Geom& g, const Bufs& b, cudaStream_t s) {
@@ -1500,7 +1500,7 @@ cudaError_t prepare_refine(Geom& g) {
   cudaError_t e = cudaFuncSetAttribute(k_refine, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
   g.ncl = 16;
-  e = cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)refine_smem_max(g));
+  e = raise_smem_limit((const void*)k_refine, (size_t)(refine_smem_max(g)));
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(g.ncl * g.n);
@@ -1517,7 +1517,7 @@ cudaError_t prepare_refine(Geom& g) {
   if (cudaOccupancyMaxActiveClusters(&nclusters, k_refine, &cfg) != cudaSuccess || nclusters < 1) {
     cudaGetLastError();
     g.ncl = 8;
-    e = cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)refine_smem_max(g));
+    e = raise_smem_limit((const void*)k_refine, (size_t)(refine_smem_max(g)));
   }
   return e;
 }

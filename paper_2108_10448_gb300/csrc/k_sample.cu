@@ -282,9 +282,12 @@ __global__ void k_commit(Geom g, Bufs b, unsigned long long handle, int use_hand
   TL_END(12);
 }
 
-__global__ void k_gate(Bufs b, unsigned long long handle) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  cudaGraphSetConditional((cudaGraphConditionalHandle)handle, b.st->cont ? 1u : 0u);
+// Batched solve: the loop continues while any problem of the batch continues.
+__global__ void k_batch_any(State* const* sts, int count, unsigned long long handle) {
+  int any = 0;
+  for (int i = threadIdx.x; i < count; i += 32) any |= sts[i]->cont;
+  any = __any_sync(0xffffffffu, any);
+  if (threadIdx.x == 0) cudaGraphSetConditional((cudaGraphConditionalHandle)handle, any ? 1u : 0u);
 }
 
 int grid_for(long long work) {
@@ -329,7 +332,7 @@ cudaError_t launch_commit(const Geom& g, const Bufs& b, unsigned long long handl
   return cudaGetLastError();
 }
 
-cudaError_t launch_gate(const Bufs& b, unsigned long long handle, cudaStream_t s) {
-  k_gate<<<1, 32, 0, s>>>(b, handle);
+cudaError_t launch_batch_any(State* const* sts, int count, unsigned long long handle, cudaStream_t s) {
+  k_batch_any<<<1, 32, 0, s>>>(sts, count, handle);
   return cudaGetLastError();
 }

@@ -17,6 +17,7 @@
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <mutex>
 
 #define RT_MAXN 4
 #define RT_MAXR 16
@@ -168,6 +169,19 @@ cudaError_t prepare_backward(int max_m);
 cudaError_t launch_backward(const Geom& g, const Bufs& b, const BwWork& w, int K, const float* dL,
                             float* dX, cudaStream_t s);
 
+// Raises (never lowers) a kernel's dynamic shared-memory limit. The limit is a property of the
+// function, shared by every plan in the process, so plans that coexist (a batch, say) must not
+// shrink one another's.
+inline cudaError_t raise_smem_limit(const void* f, size_t bytes) {
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, f);
+  if (e != cudaSuccess) return e;
+  if ((size_t)a.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 enum { TK_SAMPLE = 0, TK_ERR = 1, TK_DENSE = 2, TK_MAXABS = 3, TK_COUNT = 8 };
 
 // ---------------------------------------------------------------- host launch wrappers
@@ -185,7 +199,7 @@ cudaError_t launch_table(const Geom& g, const Bufs& b, int next, cudaStream_t s)
 cudaError_t launch_sample_err(const Geom& g, const Bufs& b, cudaStream_t s);
 cudaError_t launch_commit(const Geom& g, const Bufs& b, unsigned long long handle, int use_handle,
                           cudaStream_t s);
-cudaError_t launch_gate(const Bufs& b, unsigned long long handle, cudaStream_t s);
+cudaError_t launch_batch_any(State* const* sts, int count, unsigned long long handle, cudaStream_t s);
 cudaError_t launch_dense(const Geom& g, const Bufs& b, int form, cudaStream_t s);
 cudaError_t prepare_dense(const Geom& g);  // kernel attributes of the dense pass (call at create)
 bool dense_form_supported(const Geom& g, int form);

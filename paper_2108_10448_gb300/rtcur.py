@@ -62,6 +62,8 @@ def load(path=LIB_PATH):
     lib.rtcur_finish.argtypes = [P, P, P, C.POINTER(rtcur_result), P]
     lib.rtcur_threshold_dense.argtypes = [P, C.c_int32, P]
     lib.rtcur_backward.argtypes = [P, P, P, P]
+    lib.rtcur_solve_batched.argtypes = [C.POINTER(P), C.c_int32, C.POINTER(P), C.POINTER(P),
+                                        C.POINTER(P), C.POINTER(P), P, P]
     lib.rtcur_threshold_dense_noalloc.argtypes = [C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
                                                   P, P, P, C.c_double, P, C.POINTER(C.c_double), P]
     lib.rtcur_threshold_dense_noalloc.restype = C.c_int
@@ -74,7 +76,7 @@ def load(path=LIB_PATH):
     lib.rtcur_destroy.argtypes = [P]
     lib.rtcur_destroy.restype = None
     for f in ("rtcur_create", "rtcur_solve", "rtcur_begin", "rtcur_iterate", "rtcur_finish",
-              "rtcur_get_factors", "rtcur_threshold_dense", "rtcur_backward"):
+              "rtcur_get_factors", "rtcur_threshold_dense", "rtcur_backward", "rtcur_solve_batched"):
         getattr(lib, f).restype = C.c_int
     _lib = lib
     return lib
@@ -187,6 +189,24 @@ def rtcur_finish(plan, L_ptr=0, S_ptr=0, stream=0, max_iter=1000):
 
 def rtcur_threshold_dense(plan, n_launch=1, stream=0):
     _check(load().rtcur_threshold_dense(plan, int(n_launch), stream or None), plan)
+
+
+def rtcur_solve_batched(plans, X_ptrs, idxs, L_ptrs=None, S_ptrs=None, stream=0, max_iter=1000):
+    """Solve len(plans) problems in one graph launch. Returns one Result per problem."""
+    lib = load()
+    n = len(plans)
+    P = C.c_void_p
+    pa = (P * n)(*plans)
+    xa = (P * n)(*X_ptrs)
+    keep = [_idx_ptr(ix) for ix in idxs]
+    ia = (P * n)(*[C.cast(ip, P) for _, ip in keep])
+    la = (P * n)(*(L_ptrs or [0] * n)) if L_ptrs else None
+    sa = (P * n)(*(S_ptrs or [0] * n)) if S_ptrs else None
+    structs = [_result_struct(max_iter) for _ in range(n)]
+    ra = (rtcur_result * n)(*[s[0] for s in structs])
+    st = lib.rtcur_solve_batched(pa, n, xa, ia, la, sa, C.cast(ra, P), stream or None)
+    _check(st, plans[0])
+    return [Result(ra[i], *structs[i][1:], ra[i].status) for i in range(n)]
 
 
 def rtcur_backward(plan, dL_ptr, dX_ptr, stream=0):
