@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the per-form comparison")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched-form comparison (64 uneven problems)")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint timing")
     return ap.parse_args()
 
 
@@ -196,6 +199,102 @@ def run_reference(a, rank, world):
         "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def run_batched(dev):
+    """Batched form on 64 uneven 3-mode problems (dims U{64..320}, ranks U{2..10}, outliers
+    10-40%, RTCUR-R, v = 3, tol 1e-5): 64 sequential rtcur_solve calls against one
+    rtcur_solve_batched graph launch with the same plans, then the autotuned configuration."""
+    import torch
+    from paper_2108_10448_gb300 import autotune
+    from paper_2108_10448_gb300 import rtcur as rt
+    from paper_2108_10448_gb300 import synth
+    probs = synth.make_batched_problems(64)
+    X = [torch.from_numpy(p.X).to(dev) for p in probs]
+    idx = [synth.pack_index_sets(synth.draw_index_sets(p.dims, p.m, p.q, seed=b, n_sets=p.max_iter))
+           for b, p in enumerate(probs)]
+    plans = [rt.rtcur_create(p.dims, p.ranks, p.m, p.q, p.zeta0, p.gamma, p.tol, p.max_iter,
+                             rt.VARIANT_R, rt.make_options()) for p in probs]
+    s = torch.cuda.current_stream(dev).cuda_stream
+    xp = [x.data_ptr() for x in X]
+    try:
+        for b, pl in enumerate(plans):  # warm: builds each plan's graphs
+            rt.rtcur_solve(pl, xp[b], idx[b], 0, 0, s, max_iter=probs[b].max_iter)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        seq = [rt.rtcur_solve(pl, xp[b], idx[b], 0, 0, s, max_iter=probs[b].max_iter)
+               for b, pl in enumerate(plans)]
+        torch.cuda.synchronize()
+        seq_s = time.perf_counter() - t0
+        rt.rtcur_solve_batched(plans, xp, idx, None, None, s, max_iter=100)  # builds the graph
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bat = rt.rtcur_solve_batched(plans, xp, idx, None, None, s, max_iter=100)
+        torch.cuda.synchronize()
+        bat_s = time.perf_counter() - t0
+    finally:
+        for pl in plans:
+            rt.rtcur_destroy(pl)
+    same = all(x.iters == y.iters and x.e == y.e for x, y in zip(seq, bat))
+    tuned = autotune.tune_batch(X, [p.dims for p in probs], [p.ranks for p in probs],
+                                [p.zeta0 for p in probs], variant="R", tol=1e-5, max_iter=100)
+    return {
+        "workload": "64 uneven 3-mode FP32 problems, dims U{64..320}, ranks U{2..10}, outliers "
+                    "U[10%, 40%], RTCUR-R, v=3, tol 1e-5 (seeds 0..63)",
+        "elements": int(sum(p.X.size for p in probs)),
+        "sequential_s": seq_s, "batched_s": bat_s, "speedup": seq_s / bat_s,
+        "problems_per_s_batched": len(probs) / bat_s,
+        "iters_total": int(sum(r.iters for r in bat)),
+        "all_converged": all(r.status == rt.OK for r in bat),
+        "batched_equals_sequential": same,
+        "tuned": {"cluster": tuned["cluster"], "upsilon": tuned["upsilon"],
+                  "graph_ms": tuned["ms"], "table": tuned["table"]},
+        "timing": "wall clock around the public calls (index upload, graph launch, results)",
+    }
+
+
+def run_adjoint(dev):
+    """Adjoint workload: K = 10 unrolled RTCUR-F iterations on 200^3, rank (5,5,5), 20% outliers;
+    device time of the forward (with checkpoints) and of rtcur_backward."""
+    import torch
+    from paper_2108_10448_gb300 import rtcur as rt
+    from paper_2108_10448_gb300 import synth
+    K = 10
+    p = synth.make_tucker_problem((200, 200, 200), (5, 5, 5), 0.2, 3.0, seed=0, keep_truth=True)
+    sets = synth.draw_index_sets(p.dims, p.m, p.q, seed=0)
+    idx = synth.pack_index_sets(sets)
+    plan = rt.rtcur_create(p.dims, p.ranks, p.m, p.q, p.zeta0, p.gamma, 0.0, K, rt.VARIANT_F,
+                           rt.make_options(checkpoint=K))
+    X = torch.from_numpy(p.X).to(dev)
+    L = torch.empty_like(X)
+    dL = torch.empty_like(X)
+    dX = torch.empty_like(X)
+    Ls = torch.from_numpy(p.L_star.astype(np.float32)).to(dev)
+    st = torch.cuda.current_stream(dev)
+    s = st.cuda_stream
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    fw, bw = [], []
+    try:
+        for rep in range(4):
+            e0.record(st)
+            rt.rtcur_begin(plan, X.data_ptr(), idx, 0, s)
+            rt.rtcur_iterate(plan, K, s)
+            rt.rtcur_finish(plan, L.data_ptr(), 0, s, max_iter=K)
+            e1.record(st)
+            torch.mul(torch.sub(L, Ls), 2.0, out=dL)
+            rt.rtcur_backward(plan, dL.data_ptr(), dX.data_ptr(), s)
+            e2.record(st)
+            torch.cuda.synchronize()
+            if rep:
+                fw.append(e0.elapsed_time(e1))
+                bw.append(e1.elapsed_time(e2))
+    finally:
+        rt.rtcur_destroy(plan)
+    return {"workload": "K=10 unrolled RTCUR-F, 200^3 FP32, rank (5,5,5), 20% outliers, "
+                        "loss ||L_K - L*||_F^2",
+            "forward_ms": float(np.median(fw)), "backward_ms": float(np.median(bw)),
+            "includes": "forward: begin + 10 iterations + L materialisation; backward: "
+                        "seed dL + rtcur_backward (FP64 pinv adjoints)"}
 
 
 def run_ours(a, rank, world):
@@ -350,6 +449,8 @@ def run_ours(a, rank, world):
         "roofline": roof,
         "forms": forms_out,
         "gpu_launches": launches_per_iter * K,
+        "batched": None if (a.no_batched or world > 1) else run_batched(dev),
+        "adjoint": None if (a.no_adjoint or world > 1) else run_adjoint(dev),
         "clocks": clk.summary(),
     }
     if not a.no_cpu_baseline:

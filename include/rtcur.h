@@ -81,7 +81,10 @@ typedef struct rtcur_options {
                                 (their sampled values X - S and HT masks, 5 B per sampled entry
                                 per iteration); 0 = off (default). Requires n_modes == 3 and
                                 checkpoint <= max_iter. */
-  int32_t reserved[6];       /* must be zero */
+  int32_t refine_cluster;    /* CTAs per mode in the FP64 pinv refinement (a thread-block
+                                cluster): 0 = auto (16, else 8), or 2, 4, 8, 16; smaller clusters
+                                suit many concurrent problems (the batched form) */
+  int32_t reserved[5];       /* must be zero */
 } rtcur_options;
 
 typedef struct rtcur_result {

@@ -263,7 +263,7 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
   o.inband_rel = 1e-6;
   if (opt) {
     o = *opt;
-    for (int i = 0; i < 6; ++i)
+    for (int i = 0; i < 5; ++i)
       if (o.reserved[i] != 0) return fail(nullptr, RTCUR_EINVAL, "options.reserved must be zero");
     if (o.refine_steps == 0 && o.jacobi_max_sweeps == 0 && o.inband_rel == 0.0) {
       o.refine_steps = 2; o.jacobi_max_sweeps = 30; o.inband_rel = 1e-6;
@@ -275,6 +275,9 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
   if (o.jacobi_max_sweeps < 1 || o.jacobi_max_sweeps > 100) return fail(nullptr, RTCUR_EINVAL, "jacobi_max_sweeps must be in [1, 100]");
   if (!(o.inband_rel >= 0.0 && o.inband_rel < 1.0)) return fail(nullptr, RTCUR_EINVAL, "inband_rel must be in [0, 1)");
   if (o.eig_method != 0 && o.eig_method != 1) return fail(nullptr, RTCUR_EINVAL, "eig_method must be 0 (tridiagonal) or 1 (Jacobi)");
+  if (o.refine_cluster != 0 && o.refine_cluster != 2 && o.refine_cluster != 4 && o.refine_cluster != 8 &&
+      o.refine_cluster != 16)
+    return fail(nullptr, RTCUR_EINVAL, "refine_cluster must be 0 (auto), 2, 4, 8 or 16");
   if (o.checkpoint < 0 || o.checkpoint > max_iter) return fail(nullptr, RTCUR_EINVAL, "checkpoint must be in [0, max_iter]");
   if (o.checkpoint > 0 && n_modes != 3) return fail(nullptr, RTCUR_EINVAL, "checkpoint (the adjoint) needs n_modes == 3");
 
@@ -493,7 +496,14 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
     e = prepare_jacobi(sm);
   }
   if (e == cudaSuccess) e = prepare_dense(g);
-  if (e == cudaSuccess) e = prepare_refine(p->g);
+  if (e == cudaSuccess) {
+    e = prepare_refine(p->g, o.refine_cluster);
+    if (e == cudaErrorInvalidValue) {
+      fail(nullptr, RTCUR_EINVAL, "refine_cluster %d cannot run for these sample sizes", o.refine_cluster);
+      rtcur_destroy(p);
+      return RTCUR_EINVAL;
+    }
+  }
   if (e == cudaSuccess) e = cudaMemset(b.ticket, 0, sizeof(unsigned) * TK_COUNT);
   if (e != cudaSuccess) {
     rtcur_status st = (e == cudaErrorMemoryAllocation) ? RTCUR_ENOMEM : RTCUR_ECUDA;

@@ -1494,11 +1494,38 @@ size_t refine_smem_max(const Geom& g) {
   return mx;
 }
 
-// Chooses the cluster size of the refinement (16 CTAs per mode when the device can schedule
-// such clusters, else 8) and sets the kernel's attributes. Updates g.ncl.
-cudaError_t prepare_refine(Geom& g) {
+// Chooses the cluster size of the refinement (`want` CTAs per mode when given, else 16 when the
+// device can schedule such clusters, else 8) and sets the kernel's attributes. Updates g.ncl.
+// Returns cudaErrorInvalidValue when the requested size cannot run (shared memory or occupancy).
+cudaError_t prepare_refine(Geom& g, int want) {
   cudaError_t e = cudaFuncSetAttribute(k_refine, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
+  if (want > 0) {
+    g.ncl = want;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (refine_smem_max(g) > (size_t)optin) return cudaErrorInvalidValue;
+    e = raise_smem_limit((const void*)k_refine, (size_t)(refine_smem_max(g)));
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(g.ncl * g.n);
+    cfg.blockDim = dim3(kRefThreads);
+    cfg.dynamicSmemBytes = refine_smem_max(g);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = g.ncl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_refine, &cfg) != cudaSuccess || nclusters < 1) {
+      cudaGetLastError();
+      return cudaErrorInvalidValue;
+    }
+    return cudaSuccess;
+  }
   g.ncl = 16;
   e = raise_smem_limit((const void*)k_refine, (size_t)(refine_smem_max(g)));
   if (e != cudaSuccess) return e;

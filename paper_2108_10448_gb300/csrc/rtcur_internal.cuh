@@ -209,7 +209,7 @@ cudaError_t launch_materialize(const Geom& g, const Bufs& b, float* L_out, float
                                cudaStream_t s);
 size_t jacobi_smem_bytes(int m);
 cudaError_t prepare_jacobi(size_t smem);
-cudaError_t prepare_refine(Geom& g);  // cluster size and shared-memory limit of the refinement  // sets the kernel's dynamic shared-memory limit
+cudaError_t prepare_refine(Geom& g, int want);  // cluster size (g.ncl) and shared-memory limit of the refinement
 
 // ---------------------------------------------------------------- device helpers
 #ifdef __CUDACC__

@@ -22,7 +22,7 @@ FLAG_RANK_DEFICIENT, FLAG_TIE = 1, 2
 class rtcur_options(C.Structure):
     _fields_ = [("scope", C.c_int32), ("dense_form", C.c_int32), ("refine_steps", C.c_int32),
                 ("jacobi_max_sweeps", C.c_int32), ("inband_rel", C.c_double),
-                ("eig_method", C.c_int32), ("checkpoint", C.c_int32), ("reserved", C.c_int32 * 6)]
+                ("eig_method", C.c_int32), ("checkpoint", C.c_int32), ("refine_cluster", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class rtcur_result(C.Structure):
@@ -104,11 +104,12 @@ EIG_TRIDIAGONAL, EIG_JACOBI = 0, 1
 
 
 def make_options(scope=SCOPE_SAMPLED, dense_form=FORM_FP32, refine_steps=2, jacobi_max_sweeps=30,
-                 inband_rel=1e-6, eig_method=EIG_TRIDIAGONAL, checkpoint=0):
+                 inband_rel=1e-6, eig_method=EIG_TRIDIAGONAL, checkpoint=0, refine_cluster=0):
     o = rtcur_options()
     o.scope, o.dense_form, o.refine_steps = scope, dense_form, refine_steps
     o.jacobi_max_sweeps, o.inband_rel, o.eig_method = jacobi_max_sweeps, inband_rel, eig_method
     o.checkpoint = checkpoint
+    o.refine_cluster = refine_cluster
     return o
 
 

@@ -110,3 +110,22 @@ def test_batched_matches_oracle(batch, i):
     ref = O.rtcur(p.X, p.ranks, sets, p.zeta0, p.gamma, p.tol, MAXIT, variant, keep_full=True)
     assert batch["res_b"][i].iters == ref["iters"]
     assert rel_fro(batch["Lb"][i].astype(np.float64), ref["L"]) <= 1e-5
+
+
+def test_autotuner_picks_a_converging_configuration(tmp_path):
+    import torch
+    from paper_2108_10448_gb300 import autotune
+    probs = [synth.make_tucker_problem(d, r, 0.2, 3.0, seed=s)
+             for d, r, s in (((40, 36, 44), (2, 3, 2), 20), ((52, 40, 30), (3, 2, 2), 21))]
+    X = [torch.from_numpy(p.X).cuda() for p in probs]
+    cache = str(tmp_path / "tune.json")
+    out = autotune.tune_batch(X, [p.dims for p in probs], [p.ranks for p in probs],
+                              [p.zeta0 for p in probs], variant="R", clusters=(4, 16),
+                              upsilons=(3.0,), cache_path=cache)
+    assert out["cluster"] in (4, 16) and out["upsilon"] == 3.0
+    assert len(out["table"]) == 2 and all(r.get("converged") for r in out["table"])
+    assert out["ms"] == min(r["ms"] for r in out["table"])
+    again = autotune.tune_batch(X, [p.dims for p in probs], [p.ranks for p in probs],
+                                [p.zeta0 for p in probs], variant="R", clusters=(4, 16),
+                                upsilons=(3.0,), cache_path=cache)
+    assert again == out  # served from the cache
