@@ -215,12 +215,14 @@ __global__ void k_bw_scatter_rows(double* Ab, const double* Pb, const long long*
   Ab[I[a] * m + c] += Pb[e];
 }
 
-// Per slot: X receives the unmasked adjoint, L^(k) the masked one.
+// Slots [e0, e1) of one segment (R, or the fibers of one mode): X receives the unmasked adjoint,
+// L^(k) the masked one. Positions are distinct within a segment, so segments launched one after
+// another add into dX without atomics, in a fixed order.
 __global__ void k_bw_slots(Geom g, const long long* set, const unsigned char* mask, const double* Vb,
-                           double* Lb, double* dX) {
+                           double* Lb, double* dX, long long e0, long long e1) {
   long long p[RT_MAXN];
   const long long stride = (long long)gridDim.x * kT;
-  for (long long e = (long long)blockIdx.x * kT + threadIdx.x; e < g.nS; e += stride) {
+  for (long long e = e0 + (long long)blockIdx.x * kT + threadIdx.x; e < e1; e += stride) {
     const double v = Vb[e];
     if (mask[e]) {
       Lb[e] = v;
@@ -229,9 +231,31 @@ __global__ void k_bw_slots(Geom g, const long long* set, const unsigned char* ma
       sample_coords(g, set, e, p);
       long long lin = 0;
       for (int l = 0; l < g.n; ++l) lin = lin * g.d[l] + p[l];
-      atomicAdd(dX + lin, v);
+      dX[lin] += v;
     }
   }
+}
+
+// A_bar_l(t, :) += sum over the fibers c with p_l(c) = t, in ascending c, of G(c, :) (q x m_l):
+// the row scatter of the per-fiber contributions without atomics.
+__global__ void k_bw_rows_ordered(Geom g, const long long* J, int i, int l, int q, const double* Gc,
+                                  int ml, double* Ab) {
+  const long long e = (long long)blockIdx.x * kT + threadIdx.x;
+  if (e >= g.d[l] * ml) return;
+  const long long t = e / ml;
+  const int x = (int)(e % ml);
+  double acc = 0.0;
+  long long p[RT_MAXN];
+  for (int c = 0; c < q; ++c) {
+    long long j = J[c];
+    for (int l2 = g.n - 1; l2 >= 0; --l2) {
+      if (l2 == i) continue;
+      p[l2] = j % g.d[l2];
+      j /= g.d[l2];
+    }
+    if (p[l] == t) acc += Gc[(long long)c * ml + x];
+  }
+  Ab[e] += acc;
 }
 
 __global__ void k_bw_to_f32(const double* src, float* dst, long long n) {
@@ -261,7 +285,7 @@ struct FiberArgs {
   int go, ga, gb;
   int sa, sb;            // 0: row p_mode of A'_mode; 1: column c of Zfb (m_i x q)
   const double* Zfb;
-  int out_kind;          // 0: Zf[x * q + c]; 1: atomicAdd into Ab_go[p_go * m_go + x]
+  int out_kind;          // 0: out[x * q + c] (m_go x q); 1: out[c * m_go + x] (q x m_go)
   double* out;
 };
 
@@ -291,7 +315,7 @@ __global__ void __launch_bounds__(kT) k_bw_fiber(Geom g, FiberArgs f) {
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if (lane == 0) {
       if (f.out_kind == 0) f.out[(long long)x * f.q + c] = acc;
-      else atomicAdd(f.out + p[f.go] * mo + x, acc);
+      else f.out[(long long)c * mo + x] = acc;
     }
   }
 }
@@ -327,51 +351,55 @@ __global__ void __launch_bounds__(kT) k_bw_fiber_rbar(Geom g, FiberArgs f, doubl
 }
 
 // ------------------------------------------------------------------ FP64 Jacobi eigensolver
-// One CTA per symmetric m x m matrix (m <= kEigMax): parallel cyclic Jacobi with the
-// round-robin ordering (m/2 disjoint rotations per round, m-1 rounds per sweep), A in shared
-// memory, U in global memory. Output: lambda descending, U columns in the same order.
+// One CTA per symmetric PSD m x m matrix (m <= kEigMax), all recorded iterations and modes in one
+// launch: parallel cyclic Jacobi with the round-robin ordering (m/2 disjoint rotations per round,
+// m-1 rounds per sweep), A in shared memory, U in global memory. A pair is rotated only when
+// |a_pq| > 1e-15 sqrt(a_pp a_qq) (the relative test that gives PSD matrices eigenvalues to high
+// relative accuracy); the sweeps stop when one rotates nothing. Output: lambda descending, the
+// columns of U in the same order.
 constexpr int kEigMax = 160;
 
-__global__ void __launch_bounds__(kT) k_bw_eig(double* M0, double* U0, double* lam0, long long slot_mm,
-                                               long long slot_m, int m, int max_sweeps) {
+struct EigArgs {
+  double* U;        // per slot and mode: M on entry, eigenvectors on exit
+  double* lam;
+  long long offMM[RT_MAXN], offM[RT_MAXN];
+  long long slotMM, slotM;
+  int m[RT_MAXN];
+  int nmodes;
+};
+
+__global__ void __launch_bounds__(kT) k_bw_eig(EigArgs ea, int max_sweeps) {
   extern __shared__ double sA[];
   __shared__ double cs[kEigMax / 2], sn[kEigMax / 2];
   __shared__ int pp[kEigMax / 2], qq[kEigMax / 2];
-  __shared__ double red[kT / 32][2];
   __shared__ int perm[kEigMax];
-  __shared__ int done;
-  double* M = M0 + blockIdx.x * slot_mm;
-  double* U = U0 + blockIdx.x * slot_mm;
-  double* lam = lam0 + blockIdx.x * slot_m;
+  __shared__ int nrot;
+  const int slot = blockIdx.x / ea.nmodes, mode = blockIdx.x % ea.nmodes;
+  const int m = ea.m[mode];
+  double* M = ea.U + slot * ea.slotMM + ea.offMM[mode];
+  double* U = M;
+  double* lam = ea.lam + slot * ea.slotM + ea.offM[mode];
   const int mp = (m + 1) & ~1;  // padded to even; index m (if m odd) is a dummy
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int tid = threadIdx.x;
   for (int e = tid; e < mp * mp; e += kT) {
     int r = e / mp, c = e % mp;
     sA[e] = (r < m && c < m) ? M[(long long)r * m + c] : 0.0;
   }
-  __syncthreads();  // M and U may share storage: every read of M precedes the first write of U
+  __syncthreads();  // M and U share storage: every read of M precedes the first write of U
   for (int e = tid; e < m * m; e += kT) U[e] = ((e / m) == (e % m)) ? 1.0 : 0.0;
   __syncthreads();
+  // entries below 1e-17 of the largest diagonal entry are rounding noise of the FP64 Gram
+  // matrix; rotating them would keep a rank-deficient matrix sweeping forever
+  __shared__ double floor_abs;
+  if (tid == 0) {
+    double mxd = 0.0;
+    for (int j = 0; j < m; ++j) mxd = fmax(mxd, fabs(sA[j * mp + j]));
+    floor_abs = 1e-17 * mxd;
+  }
+  __syncthreads();
   for (int sw = 0; sw < max_sweeps; ++sw) {
-    double off = 0.0, tot = 0.0;
-    for (int e = tid; e < mp * mp; e += kT) {
-      double v = sA[e];
-      tot += v * v;
-      if (e / mp != e % mp) off += v * v;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      off += __shfl_down_sync(0xffffffffu, off, o);
-      tot += __shfl_down_sync(0xffffffffu, tot, o);
-    }
-    if (lane == 0) { red[wid][0] = off; red[wid][1] = tot; }
+    if (tid == 0) nrot = 0;
     __syncthreads();
-    if (tid == 0) {
-      double a0 = 0.0, a1 = 0.0;
-      for (int w = 0; w < kT / 32; ++w) { a0 += red[w][0]; a1 += red[w][1]; }
-      done = (a0 <= 1e-30 * a1) ? 1 : 0;
-    }
-    __syncthreads();
-    if (done) break;
     for (int rd = 0; rd < mp - 1; ++rd) {
       if (tid < mp / 2) {
         const int t = tid;
@@ -381,14 +409,15 @@ __global__ void __launch_bounds__(kT) k_bw_eig(double* M0, double* U0, double* l
         double c = 1.0, s = 0.0;
         if (p < m && q < m) {
           const double apq = sA[p * mp + q];
-          if (apq != 0.0) {
-            const double app = sA[p * mp + p], aqq = sA[q * mp + q];
+          const double app = sA[p * mp + p], aqq = sA[q * mp + q];
+          if (fabs(apq) > 1e-15 * sqrt(fabs(app * aqq)) && fabs(apq) > floor_abs) {
             const double th = (aqq - app) / (2.0 * apq);
             double tt;
             if (fabs(th) > 1e150) tt = 0.5 / th;
             else tt = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
             c = 1.0 / sqrt(tt * tt + 1.0);
             s = tt * c;
+            atomicAdd(&nrot, 1);
           }
         }
         pp[t] = p;
@@ -400,8 +429,10 @@ __global__ void __launch_bounds__(kT) k_bw_eig(double* M0, double* U0, double* l
       // rows: A <- G^T A
       for (int e = tid; e < (mp / 2) * mp; e += kT) {
         const int t = e / mp, col = e % mp;
+        const double s = sn[t];
+        if (s == 0.0) continue;
         const int p = pp[t], q = qq[t];
-        const double c = cs[t], s = sn[t];
+        const double c = cs[t];
         const double ap = sA[p * mp + col], aq = sA[q * mp + col];
         sA[p * mp + col] = c * ap - s * aq;
         sA[q * mp + col] = s * ap + c * aq;
@@ -410,8 +441,10 @@ __global__ void __launch_bounds__(kT) k_bw_eig(double* M0, double* U0, double* l
       // columns: A <- A G, U <- U G
       for (int e = tid; e < (mp / 2) * mp; e += kT) {
         const int t = e / mp, row = e % mp;
+        const double s = sn[t];
+        if (s == 0.0) continue;
         const int p = pp[t], q = qq[t];
-        const double c = cs[t], s = sn[t];
+        const double c = cs[t];
         const double ap = sA[row * mp + p], aq = sA[row * mp + q];
         sA[row * mp + p] = c * ap - s * aq;
         sA[row * mp + q] = s * ap + c * aq;
@@ -423,6 +456,8 @@ __global__ void __launch_bounds__(kT) k_bw_eig(double* M0, double* U0, double* l
       }
       __syncthreads();
     }
+    if (nrot == 0) break;  // uniform: read after the last barrier of the sweep
+    __syncthreads();       // nobody resets nrot before everyone has read it
   }
   // sort descending (selection on one thread; m <= kEigMax)
   if (tid == 0) {
@@ -518,10 +553,22 @@ cudaError_t launch_backward(const Geom& g, const Bufs& b, const BwWork& w, int K
                      q, 1));
     }
   }
-  for (int i = 0; i < 3; ++i) {
-    // M is read from U's slot into shared memory, U overwritten with the eigenvectors
-    k_bw_eig<<<K, kT, backward_eig_smem(g.m[i]), s>>>(w.U + w.offMM[i], w.U + w.offMM[i],
-                                                      w.lam + w.offM[i], w.slotMM, w.slotM, g.m[i], 40);
+  {
+    // every (iteration, mode) matrix at once; M is read from U's slot, U overwritten in place
+    EigArgs ea;
+    ea.U = w.U;
+    ea.lam = w.lam;
+    ea.slotMM = w.slotMM;
+    ea.slotM = w.slotM;
+    ea.nmodes = 3;
+    int mx = 0;
+    for (int i = 0; i < 3; ++i) {
+      ea.offMM[i] = w.offMM[i];
+      ea.offM[i] = w.offM[i];
+      ea.m[i] = g.m[i];
+      mx = g.m[i] > mx ? g.m[i] : mx;
+    }
+    k_bw_eig<<<K * 3, kT, backward_eig_smem(mx), s>>>(ea, 60);
     BW_CK(cudaGetLastError());
   }
   for (int k = 0; k < K; ++k) {
@@ -600,10 +647,12 @@ cudaError_t launch_backward(const Geom& g, const Bufs& b, const BwWork& w, int K
       k_bw_scatter_W<<<nblk((long long)m * q), kT, 0, s>>>(Cb, w.Wb, set + g.ioff[i], m, q, d);
       BW_CK(cudaGetLastError());
     }
-    {
-      int blocks = (int)((g.nS + kT - 1) / kT);
+    for (int sg = 0; sg <= 3; ++sg) {
+      const long long e0 = g.seg[sg], e1 = g.seg[sg + 1];
+      long long blocks = (e1 - e0 + kT - 1) / kT;
       if (blocks > 4096) blocks = 4096;
-      k_bw_slots<<<blocks, kT, 0, s>>>(g, set, b.ckM + (long long)k * g.nS, w.Vb, w.Lb, w.dX64);
+      k_bw_slots<<<(unsigned)blocks, kT, 0, s>>>(g, set, b.ckM + (long long)k * g.nS, w.Vb, w.Lb, w.dX64,
+                                                 e0, e1);
       BW_CK(cudaGetLastError());
     }
     if (k == 0) break;
@@ -672,12 +721,15 @@ cudaError_t launch_backward(const Geom& g, const Bufs& b, const BwWork& w, int K
       k_bw_fiber_rbar<<<nblk(g.nR), kT, sizeof(int) * 2 * q, s>>>(g, f, Rb);
       BW_CK(cudaGetLastError());
       // A_bar_l1 rows += R' contracted with zbar (mode i) and the A'_l2 row; same for l2
-      f.go = l1; f.ga = i; f.gb = l2; f.sa = 1; f.sb = 0; f.out_kind = 1; f.out = w.Ab + w.offDM[l1];
-      k_bw_fiber<<<q, kT, 0, s>>>(g, f);
-      BW_CK(cudaGetLastError());
-      f.go = l2; f.ga = i; f.gb = l1; f.sa = 1; f.sb = 0; f.out_kind = 1; f.out = w.Ab + w.offDM[l2];
-      k_bw_fiber<<<q, kT, 0, s>>>(g, f);
-      BW_CK(cudaGetLastError());
+      for (int side = 0; side < 2; ++side) {
+        const int lo = side ? l2 : l1, lother = side ? l1 : l2;
+        f.go = lo; f.ga = i; f.gb = lother; f.sa = 1; f.sb = 0; f.out_kind = 1; f.out = w.Zf;
+        k_bw_fiber<<<q, kT, 0, s>>>(g, f);
+        BW_CK(cudaGetLastError());
+        k_bw_rows_ordered<<<nblk(g.d[lo] * g.m[lo]), kT, 0, s>>>(g, set + g.joff[i], i, lo, q, w.Zf, g.m[lo],
+                                                                 w.Ab + w.offDM[lo]);
+        BW_CK(cudaGetLastError());
+      }
     }
   }
   int blocks = (int)((g.N + kT - 1) / kT);
