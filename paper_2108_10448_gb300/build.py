@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librtcur.so")
-SOURCES = ["api.cu", "k_sample.cu", "k_pinv.cu", "k_factor.cu", "k_dense.cu", "k_plain.cu", "noalloc.cu", "backward.cu"]
+SOURCES = ["api.cu", "k_sample.cu", "k_pinv.cu", "k_factor.cu", "k_dense.cu", "k_plain.cu", "noalloc.cu", "backward.cu", "k_umma.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden", "--expt-relaxed-constexpr"]

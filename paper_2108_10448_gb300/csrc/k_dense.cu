@@ -9,8 +9,6 @@
 // for the whole launch, so the inner loop reads only X, one broadcast row of T, and writes S.
 // Blocks use few threads per SM so that the latency-bound sampled chain, which runs
 // concurrently on its own graph branch, finds room.
-#include <cuda_bf16.h>
-
 #include "rtcur_internal.cuh"
 
 namespace {
@@ -411,280 +409,6 @@ cudaError_t tma_materialize_rn(const Geom& g, const Bufs& b, int tr, size_t smem
   return e;
 }
 
-// ---------------------------------------------------------------- tensor-core forms
-// The same TMA-fed pass with the last-mode product L = T B_n^T on the tensor cores (warp-level
-// mma, FP32 accumulation), 16-row tiles, 3 stages. Each warp owns a set of 8-column blocks and
-// keeps their B_n fragments in registers for the whole pass.
-//   BF16 form: operands split in two BF16 terms, x = hi + lo, and the three significant products
-//     T_hi B_hi + T_hi B_lo + T_lo B_hi packed along K (3 r_n <= 15 <= 16, one m16n8k16 step);
-//     the dropped T_lo B_lo term is ~2^-16 relative, so L carries ~1e-5 relative error.
-//   TF32 form: plain TF32 operands (10-bit mantissa), K = r_n <= 8 (one m16n8k8 step).
-// The thresholding and the reductions are those of the FP32 pass.
-constexpr int kMmaStages = 3;
-constexpr int kMmaRows = 16;
-constexpr int kMmaThreads = 256;
-constexpr int kMmaMaxCb = 16;  // 8-column blocks per warp (d_n <= 8 * 8 * 16 = 1024)
-
-__device__ __forceinline__ unsigned pack_bf16(float lo_elem, float hi_elem) {
-  __nv_bfloat162 v = __floats2bfloat162_rn(lo_elem, hi_elem);
-  return *reinterpret_cast<unsigned*>(&v);
-}
-__device__ __forceinline__ float bf16_hi(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
-__device__ __forceinline__ unsigned to_tf32(float x) {
-  unsigned r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
-
-// K-slot kk of the split operand for a value pair (hi, lo) arrangement:
-//   A side: [hi(0..R-1), hi(0..R-1), lo(0..R-1), 0]   B side: [hi, lo, hi, 0]
-template <int RN>
-__device__ __forceinline__ float split_a(const float* v, int kk) {
-  if (kk < RN) return bf16_hi(v[kk]);
-  if (kk < 2 * RN) return bf16_hi(v[kk - RN]);
-  if (kk < 3 * RN) { float x = v[kk - 2 * RN]; return x - bf16_hi(x); }
-  return 0.f;
-}
-template <int RN>
-__device__ __forceinline__ float split_b(const float* v, int kk) {
-  if (kk < RN) return bf16_hi(v[kk]);
-  if (kk < 2 * RN) { float x = v[kk - RN]; return x - bf16_hi(x); }
-  if (kk < 3 * RN) return bf16_hi(v[kk - 2 * RN]);
-  return 0.f;
-}
-
-template <int RN, bool TF32>
-__global__ void __launch_bounds__(kMmaThreads, 1) k_dense_mma(Geom g, Bufs b) {
-  extern __shared__ __align__(128) unsigned char dsm[];
-  __shared__ unsigned long long full[kMmaStages];
-  __shared__ double sh[32];
-  __shared__ int abort_flag;
-  const State* st = b.st;
-  const int cur = st->k & 1;
-  const double zeta = g.gamma * st->zeta;
-  const float zf = (float)zeta;
-  const float band = (float)(g.inband * zeta);
-  const float* __restrict__ X = b.sp->X;
-  float* __restrict__ S = b.sp->S;
-  const float* __restrict__ T = b.T[cur];
-  const float* __restrict__ Bn = b.B[cur] + g.offB[g.n - 1];
-  const int dn = (int)g.d[g.n - 1];
-  const long long rows = g.rowsT;
-  const long long ntiles = (rows + kMmaRows - 1) / kMmaRows;
-  float* ring = reinterpret_cast<float*>(dsm);
-  const int stage_f = kMmaRows * dn;
-  const int tstage = ((kMmaRows * RN + 3) & ~3) + 4;
-  float* tring = ring + (size_t)kMmaStages * stage_f;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  const int gid = lane >> 2, tig = lane & 3;
-  const int nblk = dn / 8;
-  // B fragments of this warp's column blocks, fixed for the launch
-  unsigned bf[kMmaMaxCb][2];
-#pragma unroll
-  for (int u = 0; u < kMmaMaxCb; ++u) {
-    const int cb = wid + u * nwarp;
-    bf[u][0] = bf[u][1] = 0u;
-    if (cb < nblk) {
-      const int col = cb * 8 + gid;
-      float bv[RN];
-#pragma unroll
-      for (int c = 0; c < RN; ++c) bv[c] = __ldg(Bn + (long long)col * RN + c);
-      if (TF32) {
-        bf[u][0] = (tig < RN) ? to_tf32(bv[tig]) : 0u;
-        bf[u][1] = (tig + 4 < RN) ? to_tf32(bv[tig + 4]) : 0u;
-      } else {
-        bf[u][0] = pack_bf16(split_b<RN>(bv, 2 * tig), split_b<RN>(bv, 2 * tig + 1));
-        bf[u][1] = pack_bf16(split_b<RN>(bv, 2 * tig + 8), split_b<RN>(bv, 2 * tig + 9));
-      }
-    }
-  }
-  if (threadIdx.x == 0) {
-    abort_flag = 0;
-    for (int i = 0; i < kMmaStages; ++i) mbar_init(&full[i], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  int issued[kMmaStages], seen[kMmaStages];
-#pragma unroll
-  for (int s2 = 0; s2 < kMmaStages; ++s2) issued[s2] = seen[s2] = 0;
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int s2 = 0; s2 < kMmaStages; ++s2) {
-      long long t = blockIdx.x + (long long)s2 * gridDim.x;
-      if (t < ntiles) {
-        long long r0 = t * kMmaRows;
-        long long nr = (r0 + kMmaRows <= rows ? kMmaRows : rows - r0);
-        unsigned bytes = (unsigned)(nr * dn * 4);
-        long long a0 = (r0 * RN) & ~3LL, a1 = ((r0 + nr) * RN + 3) & ~3LL;
-        unsigned tbytes = (unsigned)((a1 - a0) * 4);
-        mbar_expect_tx(&full[s2], bytes + tbytes);
-        bulk_g2s_stream(ring + (size_t)s2 * stage_f, X + r0 * dn, bytes, &full[s2]);
-        bulk_g2s(tring + (size_t)s2 * tstage, T + a0, tbytes, &full[s2]);
-        issued[s2] = 1;
-      }
-    }
-  }
-  float res = 0.f;
-  unsigned nnz = 0u, inb = 0u;
-  int it = 0;
-  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
-    const int s2 = it % kMmaStages;
-    const unsigned par = (unsigned)((it / kMmaStages) & 1);
-    if (!mbar_wait_bounded(&full[s2], par)) {
-      abort_flag = 1;
-    } else if (threadIdx.x == 0) {
-#pragma unroll
-      for (int s3 = 0; s3 < kMmaStages; ++s3) seen[s3] += (s3 == s2) ? 1 : 0;
-    }
-    __syncthreads();
-    if (abort_flag) break;
-    const long long r0 = t * kMmaRows;
-    const int nr = (int)(r0 + kMmaRows <= rows ? kMmaRows : rows - r0);
-    const float* tile = ring + (size_t)s2 * stage_f;
-    const float* ttile = tring + (size_t)s2 * tstage + (r0 * RN - ((r0 * RN) & ~3LL));
-    // A fragment (rows gid and gid + 8 of the tile)
-    unsigned af[4];
-    {
-      float t0v[RN], t1v[RN];
-#pragma unroll
-      for (int c = 0; c < RN; ++c) {
-        t0v[c] = (gid < nr) ? ttile[gid * RN + c] : 0.f;
-        t1v[c] = (gid + 8 < nr) ? ttile[(gid + 8) * RN + c] : 0.f;
-      }
-      if (TF32) {
-        af[0] = (tig < RN) ? to_tf32(t0v[tig]) : 0u;
-        af[1] = (tig < RN) ? to_tf32(t1v[tig]) : 0u;
-        af[2] = (tig + 4 < RN) ? to_tf32(t0v[tig + 4]) : 0u;
-        af[3] = (tig + 4 < RN) ? to_tf32(t1v[tig + 4]) : 0u;
-      } else {
-        af[0] = pack_bf16(split_a<RN>(t0v, 2 * tig), split_a<RN>(t0v, 2 * tig + 1));
-        af[1] = pack_bf16(split_a<RN>(t1v, 2 * tig), split_a<RN>(t1v, 2 * tig + 1));
-        af[2] = pack_bf16(split_a<RN>(t0v, 2 * tig + 8), split_a<RN>(t0v, 2 * tig + 9));
-        af[3] = pack_bf16(split_a<RN>(t1v, 2 * tig + 8), split_a<RN>(t1v, 2 * tig + 9));
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < kMmaMaxCb; ++u) {
-      const int cb = wid + u * nwarp;
-      if (cb >= nblk) break;
-      float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
-      if (TF32) {
-        asm volatile(
-            "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-            "{%0,%1,%2,%3};"
-            : "+f"(c0), "+f"(c1), "+f"(c2), "+f"(c3)
-            : "r"(af[0]), "r"(af[1]), "r"(af[2]), "r"(af[3]), "r"(bf[u][0]), "r"(bf[u][1]));
-      } else {
-        asm volatile(
-            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-            "{%0,%1,%2,%3};"
-            : "+f"(c0), "+f"(c1), "+f"(c2), "+f"(c3)
-            : "r"(af[0]), "r"(af[1]), "r"(af[2]), "r"(af[3]), "r"(bf[u][0]), "r"(bf[u][1]));
-      }
-      const int col = cb * 8 + 2 * tig;
-      if (gid < nr) {
-        const float2 xv = *reinterpret_cast<const float2*>(tile + gid * dn + col);
-        float2 sv;
-        ht_acc(xv.x, c0, zf, band, sv.x, res, nnz, inb);
-        ht_acc(xv.y, c1, zf, band, sv.y, res, nnz, inb);
-        __stcs(reinterpret_cast<float2*>(S + (r0 + gid) * dn + col), sv);
-      }
-      if (gid + 8 < nr) {
-        const float2 xv = *reinterpret_cast<const float2*>(tile + (gid + 8) * dn + col);
-        float2 sv;
-        ht_acc(xv.x, c2, zf, band, sv.x, res, nnz, inb);
-        ht_acc(xv.y, c3, zf, band, sv.y, res, nnz, inb);
-        __stcs(reinterpret_cast<float2*>(S + (r0 + gid + 8) * dn + col), sv);
-      }
-    }
-    __syncthreads();  // stage s2 consumed
-    if (threadIdx.x == 0) {
-      long long tn = t + (long long)kMmaStages * gridDim.x;
-      if (tn < ntiles) {
-        long long rn0 = tn * kMmaRows;
-        long long nr2 = (rn0 + kMmaRows <= rows ? kMmaRows : rows - rn0);
-        unsigned bytes = (unsigned)(nr2 * dn * 4);
-        long long a0 = (rn0 * RN) & ~3LL, a1 = ((rn0 + nr2) * RN + 3) & ~3LL;
-        unsigned tbytes = (unsigned)((a1 - a0) * 4);
-        mbar_expect_tx(&full[s2], bytes + tbytes);
-        bulk_g2s_stream(ring + (size_t)s2 * stage_f, X + rn0 * dn, bytes, &full[s2]);
-        bulk_g2s(tring + (size_t)s2 * tstage, T + a0, tbytes, &full[s2]);
-#pragma unroll
-        for (int s3 = 0; s3 < kMmaStages; ++s3) issued[s3] += (s3 == s2) ? 1 : 0;
-      }
-    }
-  }
-  if (abort_flag) {
-    if (threadIdx.x == 0) {
-      atomicExch(&b.st->err, -5);  // RTCUR_ETIMEOUT
-#pragma unroll
-      for (int s3 = 0; s3 < kMmaStages; ++s3)
-        if (issued[s3] > seen[s3]) mbar_wait_bounded(&full[s3], (unsigned)((issued[s3] - 1) & 1));
-    }
-    __syncthreads();
-  }
-  double* part = b.red + (size_t)TK_DENSE * kMaxRedBlocks * RT_RED_SLOTS;
-  double t0 = block_sum_d((double)res, sh);
-  if (threadIdx.x == 0) part[blockIdx.x * RT_RED_SLOTS + 0] = t0;
-  t0 = block_sum_d((double)nnz, sh);
-  if (threadIdx.x == 0) part[blockIdx.x * RT_RED_SLOTS + 1] = t0;
-  t0 = block_sum_d((double)inb, sh);
-  if (threadIdx.x == 0) part[blockIdx.x * RT_RED_SLOTS + 2] = t0;
-  if (last_block_arrive(b.ticket + TK_DENSE)) {
-    State* w = b.st;
-    for (int slot = 0; slot < 3; ++slot) {
-      double acc = 0.0;
-      for (unsigned i2 = threadIdx.x; i2 < gridDim.x; i2 += blockDim.x) acc += part[i2 * RT_RED_SLOTS + slot];
-      acc = block_sum_d(acc, sh);
-      if (threadIdx.x == 0) {
-        if (slot == 0) w->resid_f = acc;
-        if (slot == 1) w->nnz_f = (long long)acc;
-        if (slot == 2) w->inband_f = (long long)acc;
-      }
-    }
-    if (threadIdx.x == 0) b.ticket[TK_DENSE] = 0u;
-  }
-}
-
-// Shared memory of the tensor-core pass; 0 when it does not apply (d_n % 8, d_n > 1024 or r_n
-// beyond the form's K).
-size_t mma_smem(const Geom& g, bool tf32) {
-  const long long dn = g.d[g.n - 1];
-  if (dn % 8 != 0 || dn > 8 * 8 * kMmaMaxCb) return 0;
-  if (tf32 ? (g.rlast > 8) : (3 * g.rlast > 16)) return 0;
-  return (size_t)kMmaStages * (kMmaRows * dn * 4 + (((kMmaRows * g.rlast + 3) & ~3) + 4) * 4);
-}
-
-template <int RN, bool TF>
-cudaError_t mma_launch_rn(const Geom& g, const Bufs& b, size_t smem, cudaStream_t s, bool prepare) {
-  if (prepare) {
-    cudaError_t e = raise_smem_limit((const void*)k_dense_mma<RN, TF>, smem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_dense_mma<RN, TF>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                               cudaSharedmemCarveoutMaxShared);
-    return e;
-  }
-  long long ntiles = (g.rowsT + kMmaRows - 1) / kMmaRows;
-  int grid = (int)(ntiles < 144 ? ntiles : 144);
-  k_dense_mma<RN, TF><<<grid, kMmaThreads, smem, s>>>(g, b);
-  return cudaGetLastError();
-}
-
-template <bool TF>
-cudaError_t mma_dispatch(const Geom& g, const Bufs& b, size_t smem, cudaStream_t s, bool prepare) {
-  switch (g.rlast) {
-    case 1: return mma_launch_rn<1, TF>(g, b, smem, s, prepare);
-    case 2: return mma_launch_rn<2, TF>(g, b, smem, s, prepare);
-    case 3: return mma_launch_rn<3, TF>(g, b, smem, s, prepare);
-    case 4: return mma_launch_rn<4, TF>(g, b, smem, s, prepare);
-    case 5: return mma_launch_rn<5, TF>(g, b, smem, s, prepare);
-    case 6: return TF ? mma_launch_rn<6, TF>(g, b, smem, s, prepare) : cudaErrorNotSupported;
-    case 7: return TF ? mma_launch_rn<7, TF>(g, b, smem, s, prepare) : cudaErrorNotSupported;
-    case 8: return TF ? mma_launch_rn<8, TF>(g, b, smem, s, prepare) : cudaErrorNotSupported;
-    default: return cudaErrorNotSupported;
-  }
-}
-
 // Tile geometry of the TMA pass; returns false when the pass does not apply (d_n % 4 != 0,
 // d_n > 4096, r_n > 8).
 bool tma_geometry(const Geom& g, int& tr, size_t& smem, int& threads) {
@@ -749,20 +473,16 @@ __global__ void __launch_bounds__(256) k_materialize(Geom g, Bufs b, float* L_ou
 bool dense_form_supported(const Geom& g, int form) {
   if (form == 0) return true;
   if (form == 1) return g.n == 3 && (g.N % 4) == 0;
-  if (form == 2) return mma_smem(g, false) > 0;
-  if (form == 3) return mma_smem(g, true) > 0;
+  if (form == 2) return umma_smem(g, 0) > 0;
+  if (form == 3) return umma_smem(g, 1) > 0;
   return false;
 }
 
 cudaError_t prepare_dense(const Geom& g) {
   int tr, threads;
   size_t smem;
-  if (g.dense_form == 2 && mma_smem(g, false)) {
-    cudaError_t e = mma_dispatch<false>(g, Bufs(), mma_smem(g, false), 0, true);
-    if (e != cudaSuccess) return e;
-  }
-  if (g.dense_form == 3 && mma_smem(g, true)) {
-    cudaError_t e = mma_dispatch<true>(g, Bufs(), mma_smem(g, true), 0, true);
+  if (g.dense_form == 2 || g.dense_form == 3) {
+    cudaError_t e = prepare_umma(g, g.dense_form == 2 ? 0 : 1);
     if (e != cudaSuccess) return e;
   }
   if (!tma_geometry(g, tr, smem, threads)) return cudaSuccess;
@@ -780,8 +500,8 @@ cudaError_t prepare_dense(const Geom& g) {
 
 cudaError_t launch_dense(const Geom& g, const Bufs& b, int form, cudaStream_t s) {
   if (form == 1) return launch_plain_dense(g, b, s);
-  if (form == 2) return mma_dispatch<false>(g, b, mma_smem(g, false), s, false);
-  if (form == 3) return mma_dispatch<true>(g, b, mma_smem(g, true), s, false);
+  if (form == 2) return launch_umma(g, b, 0, s);
+  if (form == 3) return launch_umma(g, b, 1, s);
   if (form != 0) return cudaErrorNotSupported;
   {
     int tr, threads;

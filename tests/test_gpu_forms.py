@@ -17,6 +17,10 @@ from gpu_helpers import run_gpu
 pytestmark = pytest.mark.gpu
 
 BAND = {rt.FORM_FP32_PLAIN: 2e-6, rt.FORM_BF16: 1e-4, rt.FORM_TF32: 4e-3}
+# Fraction of entries whose support may differ. Near convergence zeta^(k) falls below the TF32
+# evaluation error of L (~1e-3 max|L|), so the many near-zero residuals of non-outliers sit inside
+# the TF32 band and may flip; the band containment above is the guarantee, the count a sanity cap.
+MAXFRAC = {rt.FORM_FP32_PLAIN: 1e-3, rt.FORM_BF16: 1e-3, rt.FORM_TF32: 5e-2}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -25,10 +29,19 @@ def _built():
     ge.build()
 
 
+SHAPES = [
+    ((48, 40, 64), (3, 3, 4), 21),     # whole row tiles, one partial column block
+    ((37, 45, 60), (2, 3, 5), 22),     # ragged last row tile, a partial TMA box
+    ((20, 26, 260), (3, 2, 3), 23),    # three column blocks, the last one 4 columns wide
+]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("form", [rt.FORM_FP32_PLAIN, rt.FORM_BF16, rt.FORM_TF32])
-def test_form_matches_fp32_form(form):
-    p = synth.make_tucker_problem((48, 40, 64), (3, 3, 4), 0.1, 3, seed=21, max_iter=40)
-    sets = synth.draw_index_sets(p.dims, p.m, p.q, seed=21)
+def test_form_matches_fp32_form(form, shape):
+    dims, ranks, seed = shape
+    p = synth.make_tucker_problem(dims, ranks, 0.1, 3, seed=seed, max_iter=40)
+    sets = synth.draw_index_sets(p.dims, p.m, p.q, seed=seed)
     ref, L0, S0 = run_gpu(p, sets, "F", scope=rt.SCOPE_FULL, max_iter=40)
     res, L1, S1 = run_gpu(p, sets, "F", scope=rt.SCOPE_FULL, max_iter=40, dense_form=form)
     assert res.iters == ref.iters
@@ -41,10 +54,15 @@ def test_form_matches_fp32_form(form):
     zeta = ref.zeta
     band = BAND[form] * np.max(np.abs(L0))
     assert np.all(np.abs(absD[diff] - zeta) <= band + 1e-6 * zeta), int(diff.sum())
-    assert diff.sum() <= 1e-3 * diff.size
+    assert diff.sum() <= MAXFRAC[form] * diff.size
 
 
 def test_tensor_core_forms_reject_unsupported_shapes():
-    with pytest.raises(rt.RTCURError):
-        rt.rtcur_create([20, 20, 30], [2, 2, 2], [8, 8, 8], [16, 16, 16], 1.0, 0.7, 1e-5, 5, 0,
-                        rt.make_options(scope=rt.SCOPE_FULL, dense_form=rt.FORM_BF16))
+    # d_n % 4 != 0 (TMA row stride), d_n > 1024, BF16 with 3 r_n > 16, TF32 with r_n > 8
+    for dims, ranks, form in (([20, 20, 30], [2, 2, 2], rt.FORM_BF16),
+                              ([8, 8, 1028], [2, 2, 2], rt.FORM_TF32),
+                              ([20, 20, 32], [2, 2, 6], rt.FORM_BF16),
+                              ([20, 20, 32], [2, 2, 9], rt.FORM_TF32)):
+        with pytest.raises(rt.RTCURError):
+            rt.rtcur_create(dims, ranks, [8, 8, 16], [16, 16, 16], 1.0, 0.7, 1e-5, 5, 0,
+                            rt.make_options(scope=rt.SCOPE_FULL, dense_form=form))
