@@ -438,7 +438,7 @@ def run_ours(a, rank, world):
         "config": {"workload": workload_name(a), "dims": list(p.dims), "ranks": list(p.ranks),
                    "nI": p.m, "nJ": p.q, "variant": a.variant, "scope": a.scope,
                    "dense_form": "fp32 fused (FMA last-mode product)", "pinv": "fp64",
-                   "l2": "inputs larger than L2 (X is 2.05 GB), no flush",
+                   "l2": f"inputs larger than L2 (X is {p.X.nbytes / 1e9:.2f} GB, L2 0.13 GB), no flush",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "time_to_tol": {"ms": ttt_ms, "iters": res.iters, "e": res.e, "status": res.status,
                         "warm_hits": res.warm_hits,
