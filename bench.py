@@ -201,6 +201,18 @@ def run_reference(a, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def aggregate_replicas(ms, K, world, device="cpu"):
+    """Replicas: the timed region's duration is the max over ranks, and the job's value is the
+    iterations of all ranks over it. Collective only for N > 1 (an initialised process group)."""
+    if world > 1:
+        import torch
+        t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        torch.distributed.barrier()
+    return ms, world * K / (ms / 1e3)
+
+
 def run_batched(dev):
     """Batched form on 64 uneven 3-mode problems (dims U{64..320}, ranks U{2..10}, outliers
     10-40%, RTCUR-R, v = 3, tol 1e-5): 64 sequential rtcur_solve calls against one
@@ -338,14 +350,8 @@ def run_ours(a, rank, world):
         rt.rtcur_iterate(plan, K, sh)
         ev1.record(stream)
         torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-        torch.distributed.barrier()
+    ms, value = aggregate_replicas(ev0.elapsed_time(ev1), K, world, dev)
     res_it = rt.rtcur_finish(plan, 0, 0, sh, max_iter=max_iter)
-    value = world * K / (ms / 1e3)
     # --- dominant kernel alone: the dense fused pass, same launch configuration ---
     roof = None
     if scope == rt.SCOPE_FULL:
