@@ -149,7 +149,9 @@ __global__ void __launch_bounds__(512) k_dense_fp32(Geom g, Bufs b) {
 // stay free for the concurrent sampled chain). Each CTA streams tiles of `tr` whole rows of X
 // (tr * d_n floats, ~32 KB) into a kStages-deep shared-memory ring with 1-D cp.async.bulk
 // copies completed on mbarriers; one thread per float4 column computes L from its register
-// copy of B_n and the tile's rows of T, thresholds, and stores S with streaming stores.
+// copy of B_n and the tile's rows of T, thresholds, writes S over X in the stage, and the tile
+// leaves in one 1-D bulk store. A stage is refilled once its store has read it (one tile
+// later), so the stores overlap the next tile.
 // Every mbarrier wait is bounded: on expiry the kernel records RTCUR_ETIMEOUT, drains its own
 // copies (again bounded) and returns.
 constexpr int kStages = 4;
@@ -291,7 +293,6 @@ __global__ void __launch_bounds__(1024, 1) k_dense_tma(Geom g, Bufs b, int tr, i
       const float4* tile = ring + (size_t)s * stage_f4;
       const float* ttile = tring + (size_t)s * tstage + (r0 * RN - ((r0 * RN) & ~3LL));
       for (int rr = 0; rr < nr; ++rr) {
-        const long long r = r0 + rr;
         float tv[RN];
 #pragma unroll
         for (int c = 0; c < RN; ++c) tv[c] = ttile[rr * RN + c];
@@ -314,26 +315,38 @@ __global__ void __launch_bounds__(1024, 1) k_dense_tma(Geom g, Bufs b, int tr, i
           ht_acc(xv.w, L3, zf, band, sv.w, res, nnz, inb);
           if (zero_out) sv = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        __stcs(reinterpret_cast<float4*>(S + r * dn) + c4, sv);
+        const_cast<float4*>(tile)[rr * n4 + c4] = sv;  // in place: the tile goes out in one copy
       }
     }
-    __syncthreads();  // stage s fully consumed
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // stage writes -> bulk store
+    __syncthreads();  // stage s fully consumed and holding the output rows
     if (threadIdx.x == 0) {
-      long long tn = t + (long long)kStages * gridDim.x;
-      if (tn < ntiles) {
-        long long rn0 = tn * tr;
-        long long nr2 = (rn0 + tr <= rows ? tr : rows - rn0);
-        unsigned bytes = (MODE == 1) ? 0u : (unsigned)(nr2 * dn * 4);
-        long long a0 = (rn0 * RN) & ~3LL, a1 = ((rn0 + nr2) * RN + 3) & ~3LL;
-        unsigned tbytes = (unsigned)((a1 - a0) * 4);
-        mbar_expect_tx(&full[s], bytes + tbytes);
-        if (bytes) bulk_g2s_stream(ring + (size_t)s * stage_f4, X + rn0 * dn, bytes, &full[s]);
-        bulk_g2s(tring + (size_t)s * tstage, T + a0, tbytes, &full[s]);
+      // the tile's output rows leave in one bulk copy; the stage of the previous tile, whose
+      // store has now read it, is refilled with the tile kStages ahead of that one
+      asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(S + r0 * dn),
+                   "r"(smem_u32(ring + (size_t)s * stage_f4)), "r"((unsigned)(nr * dn * 4))
+                   : "memory");
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      if (it >= 1) {
+        asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+        const int sp = (it - 1) % kStages;
+        const long long tn = t + (long long)(kStages - 1) * gridDim.x;
+        if (tn < ntiles) {
+          long long rn0 = tn * tr;
+          long long nr2 = (rn0 + tr <= rows ? tr : rows - rn0);
+          unsigned bytes = (MODE == 1) ? 0u : (unsigned)(nr2 * dn * 4);
+          long long a0 = (rn0 * RN) & ~3LL, a1 = ((rn0 + nr2) * RN + 3) & ~3LL;
+          unsigned tbytes = (unsigned)((a1 - a0) * 4);
+          mbar_expect_tx(&full[sp], bytes + tbytes);
+          if (bytes) bulk_g2s_stream(ring + (size_t)sp * stage_f4, X + rn0 * dn, bytes, &full[sp]);
+          bulk_g2s(tring + (size_t)sp * tstage, T + a0, tbytes, &full[sp]);
 #pragma unroll
-        for (int s2 = 0; s2 < kStages; ++s2) issued[s2] += (s2 == s) ? 1 : 0;
+          for (int s2 = 0; s2 < kStages; ++s2) issued[s2] += (s2 == sp) ? 1 : 0;
+        }
       }
     }
   }
+  if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // output written
   if (abort_flag) {
     // drain: wait (bounded) for every copy this CTA may still have in flight
     if (threadIdx.x == 0) {
