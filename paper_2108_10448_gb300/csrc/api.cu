@@ -479,6 +479,9 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
     AL(w.Pi, w.slotMM);
     AL(w.Zf, mq);
     AL(w.Zfb, mq);
+    AL(w.va, mq);
+    AL(w.vb, mq);
+    AL(w.kr, w.krsz);
     AL(w.tmp0, w.tmpsz);
     AL(w.tmp1, w.tmpsz);
     AL(w.dX64, g.N);

@@ -116,18 +116,123 @@ inline Opnd opd(const void* p, int f64, long long sb, long long sx, long long sk
   return o;
 }
 
+// Tiled batched product for the large contractions: the same operand description as
+// k_contract (one or two contracted indices), 64 x 64 output tiles, 16-deep K tiles staged in
+// shared memory as FP32. Inner products run in FP32 within a K tile and are accumulated across
+// K tiles in FP64 (relative error ~1e-6 however long K is). blockIdx.z = batch * nsplit + split.
+constexpr int kGM = 64, kGN = 64, kGK = 16;
+
+__global__ void __launch_bounds__(256) k_gemm_t(Opnd A, Opnd B, double* C, long long csb, long long csi,
+                                                long long csj, int nb, int ni, int nj, long long nk1,
+                                                long long nk2, double alpha, double beta, int nsplit,
+                                                double* part) {
+  __shared__ float As[kGK][kGM + 4];
+  __shared__ float Bs[kGK][kGN + 4];
+  const int b = blockIdx.z / nsplit, sp = blockIdx.z % nsplit;
+  const int i0 = blockIdx.y * kGM, j0 = blockIdx.x * kGN;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const long long K = nk1 * nk2;
+  const long long ktiles = (K + kGK - 1) / kGK;
+  const long long kt0 = ktiles * sp / nsplit, kt1 = ktiles * (sp + 1) / nsplit;
+  const long long ab = (long long)b * A.sb, bb = (long long)b * B.sb;
+  double acc64[4][4] = {};
+  for (long long kt = kt0; kt < kt1; ++kt) {
+    const long long k0 = kt * kGK;
+    for (int e = threadIdx.x; e < kGM * kGK; e += 256) {
+      const int r = e / kGK, kk = e % kGK;
+      const int gi = i0 + r;
+      const long long gk = k0 + kk;
+      float v = 0.f;
+      if (gi < ni && gk < K) {
+        const long long k1 = gk / nk2, k2 = gk - k1 * nk2;
+        v = (float)ldv(A, ab + gi * A.sx + k1 * A.sk1 + k2 * A.sk2);
+      }
+      As[kk][r] = v;
+    }
+    for (int e = threadIdx.x; e < kGK * kGN; e += 256) {
+      const int kk = e / kGN, c = e % kGN;
+      const int gj = j0 + c;
+      const long long gk = k0 + kk;
+      float v = 0.f;
+      if (gj < nj && gk < K) {
+        const long long k1 = gk / nk2, k2 = gk - k1 * nk2;
+        v = (float)ldv(B, bb + gj * B.sx + k1 * B.sk1 + k2 * B.sk2);
+      }
+      Bs[kk][c] = v;
+    }
+    __syncthreads();
+    float acc[4][4] = {};
+#pragma unroll
+    for (int kk = 0; kk < kGK; ++kk) {
+      float a[4], w[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = As[kk][ty * 4 + u];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) w[v] = Bs[kk][tx * 4 + v];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a[u], w[v], acc[u][v]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc64[u][v] += (double)acc[u][v];
+    __syncthreads();
+  }
+  const long long nout = (long long)nb * ni * nj;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int gi = i0 + ty * 4 + u;
+    if (gi >= ni) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int gj = j0 + tx * 4 + v;
+      if (gj >= nj) continue;
+      if (nsplit > 1) {
+        part[(long long)sp * nout + ((long long)b * ni + gi) * nj + gj] = acc64[u][v];
+      } else {
+        double* c = C + b * csb + gi * csi + gj * csj;
+        *c = alpha * acc64[u][v] + (beta != 0.0 ? beta * *c : 0.0);
+      }
+    }
+  }
+}
+
+cudaError_t gemm(const Ctx& cx, const Opnd& A, const Opnd& B, double* C, long long csb, long long csi,
+                 long long csj, int nb, int ni, int nj, long long nk1, long long nk2, double alpha = 1.0,
+                 double beta = 0.0) {
+  const long long nout = (long long)nb * ni * nj;
+  if (nout == 0) return cudaSuccess;
+  const long long tiles = (long long)nb * ((ni + kGM - 1) / kGM) * ((nj + kGN - 1) / kGN);
+  const long long ktiles = (nk1 * nk2 + kGK - 1) / kGK;
+  long long want = (4LL * 152) / tiles;  // about four blocks per SM
+  int nsplit = (int)(want < 1 ? 1 : (want > ktiles ? ktiles : want));
+  if (nsplit > 64) nsplit = 64;
+  while (nsplit > 1 && (long long)nsplit * nout > cx.partsz) --nsplit;
+  if (nsplit < 1) nsplit = 1;
+  if ((long long)nb * nsplit > 65535) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)((nj + kGN - 1) / kGN), (unsigned)((ni + kGM - 1) / kGM), (unsigned)(nb * nsplit));
+  k_gemm_t<<<grid, 256, 0, cx.s>>>(A, B, C, csb, csi, csj, nb, ni, nj, nk1, nk2, alpha, beta, nsplit, cx.part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || nsplit == 1) return e;
+  k_contract_reduce<<<(unsigned)((nout + kT - 1) / kT), kT, 0, cx.s>>>(cx.part, nsplit, C, csb, csi, csj, nb,
+                                                                      ni, nj, alpha, beta);
+  return cudaGetLastError();
+}
+
 // Y = X x_mode M for a 3-mode tensor X (dims n, float or double), M[j][k] at M + j*mr + k*mc
 // (J rows, n[mode] columns); Y (double) has n[mode] replaced by J.
 cudaError_t ttm3(const Ctx& cx, const void* X, int xf64, const long long n[3], int mode,
                  const double* M, long long mr, long long mc, int J, double* Y, double beta = 0.0) {
   if (mode == 0) {
-    return contract(cx, opd(M, 1, 0, mr, mc), opd(X, xf64, 0, 1, n[1] * n[2]), Y, 0, n[1] * n[2], 1,
+    return gemm(cx, opd(M, 1, 0, mr, mc), opd(X, xf64, 0, 1, n[1] * n[2]), Y, 0, n[1] * n[2], 1,
                     1, J, (int)(n[1] * n[2]), n[0], 1, 1.0, beta);
   } else if (mode == 1) {
-    return contract(cx, opd(M, 1, 0, mr, mc), opd(X, xf64, n[1] * n[2], 1, n[2]), Y, (long long)J * n[2],
+    return gemm(cx, opd(M, 1, 0, mr, mc), opd(X, xf64, n[1] * n[2], 1, n[2]), Y, (long long)J * n[2],
                     n[2], 1, (int)n[0], J, (int)n[2], n[1], 1, 1.0, beta);
   }
-  return contract(cx, opd(X, xf64, 0, n[2], 1), opd(M, 1, 0, mr, mc), Y, 0, J, 1, 1,
+  return gemm(cx, opd(X, xf64, 0, n[2], 1), opd(M, 1, 0, mr, mc), Y, 0, J, 1, 1,
                   (int)(n[0] * n[1]), J, n[2], 1, 1.0, beta);
 }
 
@@ -135,13 +240,13 @@ cudaError_t ttm3(const Ctx& cx, const void* X, int xf64, const long long n[3], i
 cudaError_t contract_but3(const Ctx& cx, const void* X, int xf64, const long long n[3],
                           const double* Y, int m, int mode, double* out, double beta = 0.0) {
   if (mode == 0) {
-    return contract(cx, opd(X, xf64, 0, n[1] * n[2], 1), opd(Y, 1, 0, n[1] * n[2], 1), out, 0, m, 1, 1,
+    return gemm(cx, opd(X, xf64, 0, n[1] * n[2], 1), opd(Y, 1, 0, n[1] * n[2], 1), out, 0, m, 1, 1,
                     (int)n[0], m, n[1] * n[2], 1, 1.0, beta);
   } else if (mode == 1) {
-    return contract(cx, opd(X, xf64, 0, n[2], n[1] * n[2], 1), opd(Y, 1, 0, n[2], (long long)m * n[2], 1),
+    return gemm(cx, opd(X, xf64, 0, n[2], n[1] * n[2], 1), opd(Y, 1, 0, n[2], (long long)m * n[2], 1),
                     out, 0, m, 1, 1, (int)n[1], m, n[0], n[2], 1.0, beta);
   }
-  return contract(cx, opd(X, xf64, 0, 1, n[2]), opd(Y, 1, 0, 1, m), out, 0, m, 1, 1, (int)n[2], m,
+  return gemm(cx, opd(X, xf64, 0, 1, n[2]), opd(Y, 1, 0, 1, m), out, 0, m, 1, 1, (int)n[2], m,
                   n[0] * n[1], 1, 1.0, beta);
 }
 
@@ -273,81 +378,45 @@ __device__ __forceinline__ void fiber_other(const Geom& g, int i, long long j, l
   }
 }
 
-struct FiberArgs {
-  const float* R;        // m0 x m1 x m2 (row-major)
-  long long rs[3];       // strides of R
-  int m[3];
-  const double* A[3];    // A'_l (d_l x m_l)
-  const long long* J;    // fibers of mode i
-  int i;                 // fiber mode
-  int q;
-  // contraction: output mode go; vector modes ga (source sa), gb (source sb)
-  int go, ga, gb;
-  int sa, sb;            // 0: row p_mode of A'_mode; 1: column c of Zfb (m_i x q)
-  const double* Zfb;
-  int out_kind;          // 0: out[x * q + c] (m_go x q); 1: out[c * m_go + x] (q x m_go)
-  double* out;
-};
-
-// out_go[x] = sum_{y, z} R[x @ go, y @ ga, z @ gb] va[y] vb[z] for fiber c = blockIdx.x.
-// One warp per output x; lanes over y; the z sum in FP32, the y sum in FP64.
-__global__ void __launch_bounds__(kT) k_bw_fiber(Geom g, FiberArgs f) {
-  __shared__ float va[RT_MAXM], vb[RT_MAXM];
-  const int c = blockIdx.x;
+// Rows of A'_l at the other-mode coordinates of each fiber of mode i: V[y q + c] = A'_l(p_l(c), y).
+__global__ void k_bw_fiber_rows(Geom g, const long long* J, int i, int l, int q, const double* Al, int ml,
+                                float* V) {
+  const long long e = (long long)blockIdx.x * kT + threadIdx.x;
+  if (e >= (long long)ml * q) return;
+  const int y = (int)(e / q), c = (int)(e % q);
   long long p[RT_MAXN];
-  fiber_other(g, f.i, f.J[c], p);
-  const int ma = f.m[f.ga], mb = f.m[f.gb], mo = f.m[f.go];
-  for (int t = threadIdx.x; t < ma; t += kT)
-    va[t] = (float)(f.sa == 0 ? f.A[f.ga][p[f.ga] * ma + t] : f.Zfb[(long long)t * f.q + c]);
-  for (int t = threadIdx.x; t < mb; t += kT)
-    vb[t] = (float)(f.sb == 0 ? f.A[f.gb][p[f.gb] * mb + t] : f.Zfb[(long long)t * f.q + c]);
-  __syncthreads();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const long long so = f.rs[f.go], sa = f.rs[f.ga], sbb = f.rs[f.gb];
-  for (int x = wid; x < mo; x += kT / 32) {
-    double acc = 0.0;
-    for (int y = lane; y < ma; y += 32) {
-      const float* row = f.R + x * so + y * sa;
-      float t = 0.f;
-      for (int z = 0; z < mb; ++z) t = fmaf(row[z * sbb], vb[z], t);
-      acc = fma((double)t, (double)va[y], acc);
-    }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) {
-      if (f.out_kind == 0) f.out[(long long)x * f.q + c] = acc;
-      else f.out[(long long)c * mo + x] = acc;
-    }
-  }
+  fiber_other(g, i, J[c], p);
+  V[e] = (float)Al[p[l] * ml + y];
 }
 
-// R_bar[a] += sum_c Zfb[a_i, c] A'_l1(p_l1(c), a_l1) A'_l2(p_l2(c), a_l2) over the fibers of mode i
-__global__ void __launch_bounds__(kT) k_bw_fiber_rbar(Geom g, FiberArgs f, double* Rb) {
-  extern __shared__ int pc[];  // 2 x q other-mode coordinates
-  int l1 = -1, l2 = -1;
-  for (int l = 0; l < 3; ++l)
-    if (l != f.i) { if (l1 < 0) l1 = l; else l2 = l; }
-  for (int c = threadIdx.x; c < f.q; c += kT) {
-    long long p[RT_MAXN];
-    fiber_other(g, f.i, f.J[c], p);
-    pc[c] = (int)p[l1];
-    pc[f.q + c] = (int)p[l2];
-  }
-  __syncthreads();
-  const long long nR = (long long)f.m[0] * f.m[1] * f.m[2];
+// out[x q + c] = sum_y T[(x my + y) q + c] V[y q + c]
+__global__ void k_bw_mid(const double* T, const float* V, int mx, int my, int q, double* out) {
   const long long e = (long long)blockIdx.x * kT + threadIdx.x;
-  if (e >= nR) return;
-  int a[3];
-  a[2] = (int)(e % f.m[2]);
-  a[1] = (int)((e / f.m[2]) % f.m[1]);
-  a[0] = (int)(e / ((long long)f.m[1] * f.m[2]));
-  const double* zr = f.Zfb + (long long)a[f.i] * f.q;
-  const double* A1 = f.A[l1] + a[l1];
-  const double* A2 = f.A[l2] + a[l2];
-  const int m1 = f.m[l1], m2 = f.m[l2];
+  if (e >= (long long)mx * q) return;
+  const int x = (int)(e / q), c = (int)(e % q);
   double acc = 0.0;
-  for (int c = 0; c < f.q; ++c)
-    acc = fma(zr[c], A1[(long long)pc[c] * m1] * A2[(long long)pc[f.q + c] * m2], acc);
-  Rb[e] += acc;
+  for (int y = 0; y < my; ++y) acc = fma(T[((long long)x * my + y) * q + c], (double)V[(long long)y * q + c], acc);
+  out[e] = acc;
+}
+
+// out[c my + y] = sum_x Zb[x q + c] T[(x my + y) q + c]
+__global__ void k_bw_outer_mid(const double* T, const double* Zb, int mx, int my, int q, double* out) {
+  const long long e = (long long)blockIdx.x * kT + threadIdx.x;
+  if (e >= (long long)my * q) return;
+  const int y = (int)(e / q), c = (int)(e % q);
+  double acc = 0.0;
+  for (int x = 0; x < mx; ++x) acc = fma(Zb[(long long)x * q + c], T[((long long)x * my + y) * q + c], acc);
+  out[(long long)c * my + y] = acc;
+}
+
+// Khatri-Rao columns: KR[(y q + c) mz + z] = VA[y q + c] VB[z q + c]
+__global__ void k_bw_kr(const float* VA, const float* VB, int my, int mz, int q, float* KR) {
+  const long long e = (long long)blockIdx.x * kT + threadIdx.x;
+  if (e >= (long long)my * q * mz) return;
+  const int z = (int)(e % mz);
+  const long long t = e / mz;
+  const int c = (int)(t % q), y = (int)(t / q);
+  KR[e] = VA[(long long)y * q + c] * VB[(long long)z * q + c];
 }
 
 // ------------------------------------------------------------------ FP64 Jacobi eigensolver
@@ -522,7 +591,18 @@ void backward_layout(const Geom& g, BwWork& w) {
       if (l != i) u *= g.m[l];
     if (u > t) t = u;
   }
+  // fiber products: T1, T2 (m_i x m_l x q) in tmp0/tmp1, the Khatri-Rao columns in kr
+  long long kr = 0;
+  for (int i = 0; i < 3; ++i) {
+    long long v = g.q[i];
+    for (int l = 0; l < 3; ++l)
+      if (l != i) v *= g.m[l];
+    if (v > kr) kr = v;
+    if (v / g.m[(i + 1) % 3] * g.m[i] > t) t = v / g.m[(i + 1) % 3] * g.m[i];
+    if (v / g.m[(i + 2) % 3] * g.m[i] > t) t = v / g.m[(i + 2) % 3] * g.m[i];
+  }
   w.tmpsz = t;
+  w.krsz = kr;
   w.partsz = 1LL << 22;
 }
 
@@ -688,48 +768,51 @@ cudaError_t launch_backward(const Geom& g, const Bufs& b, const BwWork& w, int K
                                                                         set + g.ioff[i], g.m[i]);
       BW_CK(cudaGetLastError());
     }
-    // fibers of each mode i
+    // fibers of each mode i: the fiber values are A'_i z_c, z_c = R' contracted on the other two
+    // modes (l1 < l2) with the rows A'_l1(p_l1(c), :), A'_l2(p_l2(c), :). As products:
+    //   T1[x][y][c] = sum_z R'[x, y, z] VB[z][c]  -> z_c = sum_y T1 VA, A_bar_l1 rows = sum_x Zb T1
+    //   T2[x][z][c] = sum_y R'[x, y, z] VA[y][c]  -> A_bar_l2 rows = sum_x Zb T2
+    //   R_bar[x, y, z] += sum_c Zb[x][c] VA[y][c] VB[z][c]
+    // (x on mode i, y on l1, z on l2).
+    const long long rs[3] = {(long long)g.m[1] * g.m[2], g.m[2], 1};
     for (int i = 0; i < 3; ++i) {
       const int m = g.m[i], q = g.q[i];
       const long long d = g.d[i];
       const double* LbC = w.Lb + g.seg[i + 1];
-      FiberArgs f;
-      f.R = Rp;
-      f.rs[0] = (long long)g.m[1] * g.m[2];
-      f.rs[1] = g.m[2];
-      f.rs[2] = 1;
-      for (int l = 0; l < 3; ++l) {
-        f.m[l] = g.m[l];
-        f.A[l] = Ap[l];
-      }
-      f.J = set + g.joff[i];
-      f.i = i;
-      f.q = q;
+      const long long* J = set + g.joff[i];
       int l1 = -1, l2 = -1;
       for (int l = 0; l < 3; ++l)
         if (l != i) { if (l1 < 0) l1 = l; else l2 = l; }
-      // z (m x q) = R' contracted with the rows of A'_l1, A'_l2
-      f.go = i; f.ga = l1; f.gb = l2; f.sa = 0; f.sb = 0; f.Zfb = nullptr; f.out_kind = 0; f.out = w.Zf;
-      k_bw_fiber<<<q, kT, 0, s>>>(g, f);
+      const int m1 = g.m[l1], m2 = g.m[l2];
+      k_bw_fiber_rows<<<nblk((long long)m1 * q), kT, 0, s>>>(g, J, i, l1, q, Ap[l1], m1, w.va);
+      BW_CK(cudaGetLastError());
+      k_bw_fiber_rows<<<nblk((long long)m2 * q), kT, 0, s>>>(g, J, i, l2, q, Ap[l2], m2, w.vb);
+      BW_CK(cudaGetLastError());
+      BW_CK(gemm(cx, opd(Rp, 0, rs[i], rs[l1], rs[l2]), opd(w.vb, 0, 0, 1, q), w.tmp0, (long long)m1 * q, q, 1,
+                 m, m1, q, m2, 1));
+      k_bw_mid<<<nblk((long long)m * q), kT, 0, s>>>(w.tmp0, w.va, m, m1, q, w.Zf);
       BW_CK(cudaGetLastError());
       // A_bar_i += LbC Z^T; Z_bar = A'_i^T LbC
       BW_CK(contract(cx, opd(LbC, 1, 0, 1, d), opd(w.Zf, 1, 0, q, 1), w.Ab + w.offDM[i], 0, m, 1, 1, (int)d, m,
                      q, 1, 1.0, 1.0));
       BW_CK(contract(cx, opd(Ap[i], 1, 0, 1, m), opd(LbC, 1, 0, d, 1), w.Zfb, 0, q, 1, 1, m, q, d, 1));
-      f.Zfb = w.Zfb;
-      // R_bar += sum_c zbar_c x A'_l1 row x A'_l2 row
-      k_bw_fiber_rbar<<<nblk(g.nR), kT, sizeof(int) * 2 * q, s>>>(g, f, Rb);
+      // A_bar_l1 rows
+      k_bw_outer_mid<<<nblk((long long)m1 * q), kT, 0, s>>>(w.tmp0, w.Zfb, m, m1, q, w.Wb);
       BW_CK(cudaGetLastError());
-      // A_bar_l1 rows += R' contracted with zbar (mode i) and the A'_l2 row; same for l2
-      for (int side = 0; side < 2; ++side) {
-        const int lo = side ? l2 : l1, lother = side ? l1 : l2;
-        f.go = lo; f.ga = i; f.gb = lother; f.sa = 1; f.sb = 0; f.out_kind = 1; f.out = w.Zf;
-        k_bw_fiber<<<q, kT, 0, s>>>(g, f);
-        BW_CK(cudaGetLastError());
-        k_bw_rows_ordered<<<nblk(g.d[lo] * g.m[lo]), kT, 0, s>>>(g, set + g.joff[i], i, lo, q, w.Zf, g.m[lo],
-                                                                 w.Ab + w.offDM[lo]);
-        BW_CK(cudaGetLastError());
-      }
+      k_bw_rows_ordered<<<nblk(g.d[l1] * m1), kT, 0, s>>>(g, J, i, l1, q, w.Wb, m1, w.Ab + w.offDM[l1]);
+      BW_CK(cudaGetLastError());
+      // A_bar_l2 rows
+      BW_CK(gemm(cx, opd(Rp, 0, rs[i], rs[l2], rs[l1]), opd(w.va, 0, 0, 1, q), w.tmp1, (long long)m2 * q, q, 1,
+                 m, m2, q, m1, 1));
+      k_bw_outer_mid<<<nblk((long long)m2 * q), kT, 0, s>>>(w.tmp1, w.Zfb, m, m2, q, w.Wb);
+      BW_CK(cudaGetLastError());
+      k_bw_rows_ordered<<<nblk(g.d[l2] * m2), kT, 0, s>>>(g, J, i, l2, q, w.Wb, m2, w.Ab + w.offDM[l2]);
+      BW_CK(cudaGetLastError());
+      // R_bar
+      k_bw_kr<<<nblk((long long)m1 * q * m2), kT, 0, s>>>(w.va, w.vb, m1, m2, q, w.kr);
+      BW_CK(cudaGetLastError());
+      BW_CK(gemm(cx, opd(w.Zfb, 1, 0, q, 1), opd(w.kr, 0, (long long)q * m2, 1, m2), Rb, rs[l1], rs[i], rs[l2], m1,
+                 m, m2, q, 1, 1.0, 1.0));
     }
   }
   int blocks = (int)((g.N + kT - 1) / kT);

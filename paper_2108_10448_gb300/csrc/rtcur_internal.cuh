@@ -159,6 +159,8 @@ struct BwWork {
   double* Lb;    // nS: adjoint of L^(k) at the slots
   double* Ab;    // slotDM: A_bar_i
   double *Pb, *Wb, *T0, *T1, *Pi, *Zf, *Zfb;
+  float *va, *vb, *kr;  // fiber rows of the two other modes (m x q) and their Khatri-Rao product
+  long long krsz;
   double *tmp0, *tmp1;  // tmpsz each
   double* dX64;  // N
   double* part;  // partsz: split-K partial sums
