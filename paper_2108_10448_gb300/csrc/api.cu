@@ -465,6 +465,7 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
     }
     AL(w.W, K * w.slotW);
     AL(w.U, K * w.slotMM);
+    AL(w.Ub, K * w.slotMM);
     AL(w.lam, K * w.slotM);
     AL(w.Z, K * w.slotMM);
     AL(w.P, K * w.slotQM);
@@ -482,6 +483,7 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
     AL(w.va, mq);
     AL(w.vb, mq);
     AL(w.kr, w.krsz);
+    AL(w.pc, RT_MAXQ);
     AL(w.tmp0, w.tmpsz);
     AL(w.tmp1, w.tmpsz);
     AL(w.dX64, g.N);

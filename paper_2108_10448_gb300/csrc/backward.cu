@@ -90,7 +90,9 @@ cudaError_t contract(const Ctx& cx, const Opnd& A, const Opnd& B, double* C, lon
                      long long nk2, double alpha = 1.0, double beta = 0.0) {
   const long long nout = (long long)nb * ni * nj;
   if (nout == 0) return cudaSuccess;
-  long long want = (2LL * 152 * 1024) / nout;  // enough threads to fill the GPU
+  // few outputs: split the first contracted index so that enough threads run (each output is
+  // an FP64 dot product; unsplit, a few thousand threads would run long serial chains)
+  long long want = (2LL * 152 * 1024) / nout;
   int nsplit = (int)(want < 1 ? 1 : (want > nk1 ? nk1 : want));
   if (nsplit > 256) nsplit = 256;
   while (nsplit > 1 && (long long)nsplit * nout > cx.partsz) --nsplit;
@@ -122,10 +124,13 @@ inline Opnd opd(const void* p, int f64, long long sb, long long sx, long long sk
 // K tiles in FP64 (relative error ~1e-6 however long K is). blockIdx.z = batch * nsplit + split.
 constexpr int kGM = 64, kGN = 64, kGK = 16;
 
+template <typename TA, typename TB, bool K2>
 __global__ void __launch_bounds__(256) k_gemm_t(Opnd A, Opnd B, double* C, long long csb, long long csi,
                                                 long long csj, int nb, int ni, int nj, long long nk1,
                                                 long long nk2, double alpha, double beta, int nsplit,
                                                 double* part) {
+  const TA* __restrict__ Ap = static_cast<const TA*>(A.p);
+  const TB* __restrict__ Bp = static_cast<const TB*>(B.p);
   __shared__ float As[kGK][kGM + 4];
   __shared__ float Bs[kGK][kGN + 4];
   const int b = blockIdx.z / nsplit, sp = blockIdx.z % nsplit;
@@ -144,8 +149,12 @@ __global__ void __launch_bounds__(256) k_gemm_t(Opnd A, Opnd B, double* C, long 
       const long long gk = k0 + kk;
       float v = 0.f;
       if (gi < ni && gk < K) {
-        const long long k1 = gk / nk2, k2 = gk - k1 * nk2;
-        v = (float)ldv(A, ab + gi * A.sx + k1 * A.sk1 + k2 * A.sk2);
+        if (K2) {
+          const long long k1 = gk / nk2, k2 = gk - k1 * nk2;
+          v = (float)Ap[ab + gi * A.sx + k1 * A.sk1 + k2 * A.sk2];
+        } else {
+          v = (float)Ap[ab + gi * A.sx + gk * A.sk1];
+        }
       }
       As[kk][r] = v;
     }
@@ -155,8 +164,12 @@ __global__ void __launch_bounds__(256) k_gemm_t(Opnd A, Opnd B, double* C, long 
       const long long gk = k0 + kk;
       float v = 0.f;
       if (gj < nj && gk < K) {
-        const long long k1 = gk / nk2, k2 = gk - k1 * nk2;
-        v = (float)ldv(B, bb + gj * B.sx + k1 * B.sk1 + k2 * B.sk2);
+        if (K2) {
+          const long long k1 = gk / nk2, k2 = gk - k1 * nk2;
+          v = (float)Bp[bb + gj * B.sx + k1 * B.sk1 + k2 * B.sk2];
+        } else {
+          v = (float)Bp[bb + gj * B.sx + gk * B.sk1];
+        }
       }
       Bs[kk][c] = v;
     }
@@ -213,7 +226,14 @@ cudaError_t gemm(const Ctx& cx, const Opnd& A, const Opnd& B, double* C, long lo
   if (nsplit < 1) nsplit = 1;
   if ((long long)nb * nsplit > 65535) return cudaErrorInvalidValue;
   dim3 grid((unsigned)((nj + kGN - 1) / kGN), (unsigned)((ni + kGM - 1) / kGM), (unsigned)(nb * nsplit));
-  k_gemm_t<<<grid, 256, 0, cx.s>>>(A, B, C, csb, csi, csj, nb, ni, nj, nk1, nk2, alpha, beta, nsplit, cx.part);
+  const bool k2 = nk2 > 1;
+#define GEMM_LAUNCH(TA, TB, K2V) \
+  k_gemm_t<TA, TB, K2V><<<grid, 256, 0, cx.s>>>(A, B, C, csb, csi, csj, nb, ni, nj, nk1, nk2, alpha, beta, nsplit, cx.part)
+  if (A.f64 && B.f64) { if (k2) GEMM_LAUNCH(double, double, true); else GEMM_LAUNCH(double, double, false); }
+  else if (A.f64) { if (k2) GEMM_LAUNCH(double, float, true); else GEMM_LAUNCH(double, float, false); }
+  else if (B.f64) { if (k2) GEMM_LAUNCH(float, double, true); else GEMM_LAUNCH(float, double, false); }
+  else { if (k2) GEMM_LAUNCH(float, float, true); else GEMM_LAUNCH(float, float, false); }
+#undef GEMM_LAUNCH
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || nsplit == 1) return e;
   k_contract_reduce<<<(unsigned)((nout + kT - 1) / kT), kT, 0, cx.s>>>(cx.part, nsplit, C, csb, csi, csj, nb,
@@ -341,34 +361,6 @@ __global__ void k_bw_slots(Geom g, const long long* set, const unsigned char* ma
   }
 }
 
-// A_bar_l(t, :) += sum over the fibers c with p_l(c) = t, in ascending c, of G(c, :) (q x m_l):
-// the row scatter of the per-fiber contributions without atomics.
-__global__ void k_bw_rows_ordered(Geom g, const long long* J, int i, int l, int q, const double* Gc,
-                                  int ml, double* Ab) {
-  const long long e = (long long)blockIdx.x * kT + threadIdx.x;
-  if (e >= g.d[l] * ml) return;
-  const long long t = e / ml;
-  const int x = (int)(e % ml);
-  double acc = 0.0;
-  long long p[RT_MAXN];
-  for (int c = 0; c < q; ++c) {
-    long long j = J[c];
-    for (int l2 = g.n - 1; l2 >= 0; --l2) {
-      if (l2 == i) continue;
-      p[l2] = j % g.d[l2];
-      j /= g.d[l2];
-    }
-    if (p[l] == t) acc += Gc[(long long)c * ml + x];
-  }
-  Ab[e] += acc;
-}
-
-__global__ void k_bw_to_f32(const double* src, float* dst, long long n) {
-  const long long stride = (long long)gridDim.x * kT;
-  for (long long e = (long long)blockIdx.x * kT + threadIdx.x; e < n; e += stride) dst[e] = (float)src[e];
-}
-
-// ------------------------------------------------------------------ fiber contractions
 // Other-mode coordinates of fiber c of mode i (column J[c] of X_(i), row-major over the others).
 __device__ __forceinline__ void fiber_other(const Geom& g, int i, long long j, long long* p) {
   for (int l = g.n - 1; l >= 0; --l) {
@@ -377,6 +369,36 @@ __device__ __forceinline__ void fiber_other(const Geom& g, int i, long long j, l
     j /= g.d[l];
   }
 }
+
+// A_bar_l(t, :) += sum over the fibers c with p_l(c) = t, in ascending c, of G(c, :) (q x m_l):
+// the row scatter of the per-fiber contributions without atomics.
+__global__ void k_bw_rows_ordered(Geom g, const int* pl, int q, const double* Gc, int ml, double* Ab,
+                                  long long dl) {
+  const long long e = (long long)blockIdx.x * kT + threadIdx.x;
+  if (e >= dl * ml) return;
+  const int t = (int)(e / ml);
+  const int x = (int)(e % ml);
+  double acc = 0.0;
+  for (int c = 0; c < q; ++c)
+    if (pl[c] == t) acc += Gc[(long long)c * ml + x];
+  Ab[e] += acc;
+}
+
+// Coordinate on mode l of each fiber of mode i.
+__global__ void k_bw_fiber_coord(Geom g, const long long* J, int i, int l, int q, int* pl) {
+  const int c = blockIdx.x * kT + threadIdx.x;
+  if (c >= q) return;
+  long long p[RT_MAXN];
+  fiber_other(g, i, J[c], p);
+  pl[c] = (int)p[l];
+}
+
+__global__ void k_bw_to_f32(const double* src, float* dst, long long n) {
+  const long long stride = (long long)gridDim.x * kT;
+  for (long long e = (long long)blockIdx.x * kT + threadIdx.x; e < n; e += stride) dst[e] = (float)src[e];
+}
+
+// ------------------------------------------------------------------ fiber contractions
 
 // Rows of A'_l at the other-mode coordinates of each fiber of mode i: V[y q + c] = A'_l(p_l(c), y).
 __global__ void k_bw_fiber_rows(Geom g, const long long* J, int i, int l, int q, const double* Al, int ml,
@@ -429,7 +451,9 @@ __global__ void k_bw_kr(const float* VA, const float* VB, int my, int mz, int q,
 constexpr int kEigMax = 160;
 
 struct EigArgs {
-  double* U;        // per slot and mode: M on entry, eigenvectors on exit
+  const double* M;  // per slot and mode: the symmetric matrix
+  double* U;        // eigenvectors on exit (FP64 polish: the starting basis on entry)
+  double* W;        // FP64 polish scratch (M U)
   double* lam;
   long long offMM[RT_MAXN], offM[RT_MAXN];
   long long slotMM, slotM;
@@ -437,7 +461,7 @@ struct EigArgs {
   int nmodes;
 };
 
-__global__ void __launch_bounds__(kT) k_bw_eig(EigArgs ea, int max_sweeps) {
+__global__ void __launch_bounds__(kT) k_bw_eig(EigArgs ea, int max_sweeps, int polish) {
   extern __shared__ double sA[];
   __shared__ double cs[kEigMax / 2], sn[kEigMax / 2];
   __shared__ int pp[kEigMax / 2], qq[kEigMax / 2];
@@ -445,17 +469,36 @@ __global__ void __launch_bounds__(kT) k_bw_eig(EigArgs ea, int max_sweeps) {
   __shared__ int nrot;
   const int slot = blockIdx.x / ea.nmodes, mode = blockIdx.x % ea.nmodes;
   const int m = ea.m[mode];
-  double* M = ea.U + slot * ea.slotMM + ea.offMM[mode];
-  double* U = M;
+  const long long off = slot * ea.slotMM + ea.offMM[mode];
+  const double* M = ea.M + off;
+  double* U = ea.U + off;
   double* lam = ea.lam + slot * ea.slotM + ea.offM[mode];
   const int mp = (m + 1) & ~1;  // padded to even; index m (if m odd) is a dummy
   const int tid = threadIdx.x;
-  for (int e = tid; e < mp * mp; e += kT) {
-    int r = e / mp, c = e % mp;
-    sA[e] = (r < m && c < m) ? M[(long long)r * m + c] : 0.0;
+  if (!polish) {
+    for (int e = tid; e < mp * mp; e += kT) {
+      int r = e / mp, c = e % mp;
+      sA[e] = (r < m && c < m) ? M[(long long)r * m + c] : 0.0;
+    }
+    for (int e = tid; e < m * m; e += kT) U[e] = ((e / m) == (e % m)) ? 1.0 : 0.0;
+  } else {
+    // start from the FP32 basis: A = U^T M U (nearly diagonal), U kept as the accumulated basis
+    double* W = ea.W + off;
+    for (int e = tid; e < m * m; e += kT) {
+      const int r = e / m, c = e % m;
+      double acc = 0.0;
+      for (int a = 0; a < m; ++a) acc = fma(M[(long long)r * m + a], U[(long long)a * m + c], acc);
+      W[e] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < mp * mp; e += kT) {
+      const int r = e / mp, c = e % mp;
+      double acc = 0.0;
+      if (r < m && c < m)
+        for (int a = 0; a < m; ++a) acc = fma(U[(long long)a * m + r], W[(long long)a * m + c], acc);
+      sA[e] = acc;
+    }
   }
-  __syncthreads();  // M and U share storage: every read of M precedes the first write of U
-  for (int e = tid; e < m * m; e += kT) U[e] = ((e / m) == (e % m)) ? 1.0 : 0.0;
   __syncthreads();
   // entries below 1e-17 of the largest diagonal entry are rounding noise of the FP64 Gram
   // matrix; rotating them would keep a rank-deficient matrix sweeping forever
@@ -545,6 +588,111 @@ __global__ void __launch_bounds__(kT) k_bw_eig(EigArgs ea, int max_sweeps) {
   for (int e = tid; e < m * m; e += kT) U[e] = sA[e];
 }
 
+
+// FP32 cyclic Jacobi, A and U in shared memory (the same round-robin ordering): the starting
+// basis of the FP64 polish. A pair is rotated when |a_pq| > 1e-7 sqrt(a_pp a_qq) and above a
+// noise floor of 1e-8 of the largest diagonal entry; output lambda descending, U as FP64.
+__global__ void __launch_bounds__(kT) k_bw_eig32(EigArgs ea, int max_sweeps) {
+  extern __shared__ float sF[];
+  __shared__ float cs[kEigMax / 2], sn[kEigMax / 2];
+  __shared__ int pp[kEigMax / 2], qq[kEigMax / 2];
+  __shared__ int perm[kEigMax];
+  __shared__ int nrot;
+  __shared__ float floor_abs;
+  const int slot = blockIdx.x / ea.nmodes, mode = blockIdx.x % ea.nmodes;
+  const int m = ea.m[mode];
+  const long long off = slot * ea.slotMM + ea.offMM[mode];
+  const double* M = ea.M + off;
+  double* Uout = ea.U + off;
+  double* lam = ea.lam + slot * ea.slotM + ea.offM[mode];
+  const int mp = (m + 1) & ~1;
+  float* sA = sF;
+  float* sU = sF + mp * mp;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < mp * mp; e += kT) {
+    int r = e / mp, c = e % mp;
+    sA[e] = (r < m && c < m) ? (float)M[(long long)r * m + c] : 0.f;
+    sU[e] = (r == c) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    float mxd = 0.f;
+    for (int j = 0; j < m; ++j) mxd = fmaxf(mxd, fabsf(sA[j * mp + j]));
+    floor_abs = 1e-8f * mxd;
+  }
+  __syncthreads();
+  for (int sw = 0; sw < max_sweeps; ++sw) {
+    if (tid == 0) nrot = 0;
+    __syncthreads();
+    for (int rd = 0; rd < mp - 1; ++rd) {
+      if (tid < mp / 2) {
+        const int t = tid;
+        const int k1 = t, k2 = mp - 1 - t;
+        const int p = (k1 == 0) ? 0 : ((k1 - 1 + rd) % (mp - 1)) + 1;
+        const int q = (k2 == 0) ? 0 : ((k2 - 1 + rd) % (mp - 1)) + 1;
+        float c = 1.f, s = 0.f;
+        if (p < m && q < m) {
+          const float apq = sA[p * mp + q];
+          const float app = sA[p * mp + p], aqq = sA[q * mp + q];
+          if (fabsf(apq) > 1e-7f * sqrtf(fabsf(app * aqq)) && fabsf(apq) > floor_abs) {
+            const float th = (aqq - app) / (2.f * apq);
+            float tt;
+            if (fabsf(th) > 1e18f) tt = 0.5f / th;
+            else tt = (th >= 0.f ? 1.f : -1.f) / (fabsf(th) + sqrtf(th * th + 1.f));
+            c = 1.f / sqrtf(tt * tt + 1.f);
+            s = tt * c;
+            atomicAdd(&nrot, 1);
+          }
+        }
+        pp[t] = p;
+        qq[t] = q;
+        cs[t] = c;
+        sn[t] = s;
+      }
+      __syncthreads();
+      for (int e = tid; e < (mp / 2) * mp; e += kT) {
+        const int t = e / mp, col = e % mp;
+        const float s = sn[t];
+        if (s == 0.f) continue;
+        const int p = pp[t], q = qq[t];
+        const float c = cs[t];
+        const float ap = sA[p * mp + col], aq = sA[q * mp + col];
+        sA[p * mp + col] = c * ap - s * aq;
+        sA[q * mp + col] = s * ap + c * aq;
+      }
+      __syncthreads();
+      for (int e = tid; e < (mp / 2) * mp; e += kT) {
+        const int t = e / mp, row = e % mp;
+        const float s = sn[t];
+        if (s == 0.f) continue;
+        const int p = pp[t], q = qq[t];
+        const float c = cs[t];
+        const float ap = sA[row * mp + p], aq = sA[row * mp + q];
+        sA[row * mp + p] = c * ap - s * aq;
+        sA[row * mp + q] = s * ap + c * aq;
+        const float up = sU[row * mp + p], uq = sU[row * mp + q];
+        sU[row * mp + p] = c * up - s * uq;
+        sU[row * mp + q] = s * up + c * uq;
+      }
+      __syncthreads();
+    }
+    if (nrot == 0) break;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    for (int j = 0; j < m; ++j) perm[j] = j;
+    for (int j = 0; j < m; ++j) {
+      int best = j;
+      for (int l = j + 1; l < m; ++l)
+        if (sA[perm[l] * mp + perm[l]] > sA[perm[best] * mp + perm[best]]) best = l;
+      int t = perm[j]; perm[j] = perm[best]; perm[best] = t;
+    }
+    for (int j = 0; j < m; ++j) lam[j] = (double)sA[perm[j] * mp + perm[j]];
+  }
+  __syncthreads();
+  for (int e = tid; e < m * m; e += kT) Uout[e] = (double)sU[(e / m) * mp + perm[e % m]];
+}
+
 inline unsigned nblk(long long n) { return (unsigned)((n + kT - 1) / kT); }
 
 #define BW_CK(x)                          \
@@ -562,7 +710,9 @@ size_t backward_eig_smem(int m) {
 
 cudaError_t prepare_backward(int max_m) {
   if (max_m > kEigMax) return cudaErrorInvalidValue;
-  return raise_smem_limit((const void*)k_bw_eig, (size_t)(backward_eig_smem(max_m)));
+  cudaError_t e = raise_smem_limit((const void*)k_bw_eig, (size_t)(backward_eig_smem(max_m)));
+  if (e != cudaSuccess) return e;
+  return raise_smem_limit((const void*)k_bw_eig32, (size_t)(backward_eig_smem(max_m)));  // 2 float panels
 }
 
 void backward_layout(const Geom& g, BwWork& w) {
@@ -628,15 +778,17 @@ cudaError_t launch_backward(const Geom& g, const Bufs& b, const BwWork& w, int K
       const float* C = V(k) + g.seg[i + 1];
       k_bw_gather_W<<<nblk((long long)m * q), kT, 0, s>>>(C, set + g.ioff[i], m, q, g.d[i], Wof(k, i));
       BW_CK(cudaGetLastError());
-      // M (stored in U's slot, the eigensolver works in place from it)
-      BW_CK(contract(cx, opd(Wof(k, i), 1, 0, q, 1), opd(Wof(k, i), 1, 0, q, 1), Uof(k, i), 0, m, 1, 1, m, m,
+      // M = W W^T (in Z's slot until Z is formed)
+      BW_CK(contract(cx, opd(Wof(k, i), 1, 0, q, 1), opd(Wof(k, i), 1, 0, q, 1), Zof(k, i), 0, m, 1, 1, m, m,
                      q, 1));
     }
   }
   {
-    // every (iteration, mode) matrix at once; M is read from U's slot, U overwritten in place
+    // every (iteration, mode) matrix at once: FP32 Jacobi, then the FP64 polish from its basis
     EigArgs ea;
+    ea.M = w.Z;
     ea.U = w.U;
+    ea.W = w.Ub;
     ea.lam = w.lam;
     ea.slotMM = w.slotMM;
     ea.slotM = w.slotM;
@@ -648,7 +800,9 @@ cudaError_t launch_backward(const Geom& g, const Bufs& b, const BwWork& w, int K
       ea.m[i] = g.m[i];
       mx = g.m[i] > mx ? g.m[i] : mx;
     }
-    k_bw_eig<<<K * 3, kT, backward_eig_smem(mx), s>>>(ea, 60);
+    k_bw_eig32<<<K * 3, kT, backward_eig_smem(mx), s>>>(ea, 60);
+    BW_CK(cudaGetLastError());
+    k_bw_eig<<<K * 3, kT, backward_eig_smem(mx), s>>>(ea, 20, 1);
     BW_CK(cudaGetLastError());
   }
   for (int k = 0; k < K; ++k) {
@@ -799,14 +953,18 @@ cudaError_t launch_backward(const Geom& g, const Bufs& b, const BwWork& w, int K
       // A_bar_l1 rows
       k_bw_outer_mid<<<nblk((long long)m1 * q), kT, 0, s>>>(w.tmp0, w.Zfb, m, m1, q, w.Wb);
       BW_CK(cudaGetLastError());
-      k_bw_rows_ordered<<<nblk(g.d[l1] * m1), kT, 0, s>>>(g, J, i, l1, q, w.Wb, m1, w.Ab + w.offDM[l1]);
+      k_bw_fiber_coord<<<nblk(q), kT, 0, s>>>(g, J, i, l1, q, w.pc);
+      BW_CK(cudaGetLastError());
+      k_bw_rows_ordered<<<nblk(g.d[l1] * m1), kT, 0, s>>>(g, w.pc, q, w.Wb, m1, w.Ab + w.offDM[l1], g.d[l1]);
       BW_CK(cudaGetLastError());
       // A_bar_l2 rows
       BW_CK(gemm(cx, opd(Rp, 0, rs[i], rs[l2], rs[l1]), opd(w.va, 0, 0, 1, q), w.tmp1, (long long)m2 * q, q, 1,
                  m, m2, q, m1, 1));
       k_bw_outer_mid<<<nblk((long long)m2 * q), kT, 0, s>>>(w.tmp1, w.Zfb, m, m2, q, w.Wb);
       BW_CK(cudaGetLastError());
-      k_bw_rows_ordered<<<nblk(g.d[l2] * m2), kT, 0, s>>>(g, J, i, l2, q, w.Wb, m2, w.Ab + w.offDM[l2]);
+      k_bw_fiber_coord<<<nblk(q), kT, 0, s>>>(g, J, i, l2, q, w.pc);
+      BW_CK(cudaGetLastError());
+      k_bw_rows_ordered<<<nblk(g.d[l2] * m2), kT, 0, s>>>(g, w.pc, q, w.Wb, m2, w.Ab + w.offDM[l2], g.d[l2]);
       BW_CK(cudaGetLastError());
       // R_bar
       k_bw_kr<<<nblk((long long)m1 * q * m2), kT, 0, s>>>(w.va, w.vb, m1, m2, q, w.kr);

@@ -153,6 +153,7 @@ struct Bufs {
 // P_i = U_i^+ (q x m) and A_i = C_i P_i (d x m), all FP64; then one set of adjoint buffers.
 struct BwWork {
   double *W, *U, *lam, *Z, *P, *A;
+  double* Ub;  // per slot and mode, m x m: scratch of the FP64 eigen polish
   long long offW[RT_MAXN], offMM[RT_MAXN], offM[RT_MAXN], offQM[RT_MAXN], offDM[RT_MAXN];
   long long slotW, slotMM, slotM, slotQM, slotDM;
   double* Vb;    // nS: slot adjoint (R segment = R_bar, fiber segments = C_bar_i)
@@ -160,6 +161,7 @@ struct BwWork {
   double* Ab;    // slotDM: A_bar_i
   double *Pb, *Wb, *T0, *T1, *Pi, *Zf, *Zfb;
   float *va, *vb, *kr;  // fiber rows of the two other modes (m x q) and their Khatri-Rao product
+  int* pc;              // q: one coordinate of each fiber
   long long krsz;
   double *tmp0, *tmp1;  // tmpsz each
   double* dX64;  // N
