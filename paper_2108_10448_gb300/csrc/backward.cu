@@ -79,6 +79,37 @@ __global__ void k_contract_reduce(const double* part, int nsplit, double* C, lon
   *c = alpha * acc + (beta != 0.0 ? beta * *c : 0.0);
 }
 
+// One warp per output: the lanes split the contracted indices, then a fixed shuffle tree sums
+// them (deterministic, one launch; for the many small products of the pinv adjoint).
+__global__ void __launch_bounds__(256) k_contract_warp(Opnd A, Opnd B, double* C, long long csb,
+                                                       long long csi, long long csj, int nb, int ni, int nj,
+                                                       long long nk1, long long nk2, double alpha, double beta) {
+  const long long nout = (long long)nb * ni * nj;
+  const long long o = ((long long)blockIdx.x * 256 + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (o >= nout) return;  // uniform per warp
+  const int j = (int)(o % nj);
+  const long long t = o / nj;
+  const int i = (int)(t % ni);
+  const int b = (int)(t / ni);
+  const long long ab = b * A.sb + i * A.sx, bb = b * B.sb + j * B.sx;
+  const long long K = nk1 * nk2;
+  double acc = 0.0;
+  if (nk2 == 1) {
+    for (long long k = lane; k < K; k += 32) acc = fma(ldv(A, ab + k * A.sk1), ldv(B, bb + k * B.sk1), acc);
+  } else {
+    for (long long k = lane; k < K; k += 32) {
+      const long long k1 = k / nk2, k2 = k - k1 * nk2;
+      acc = fma(ldv(A, ab + k1 * A.sk1 + k2 * A.sk2), ldv(B, bb + k1 * B.sk1 + k2 * B.sk2), acc);
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if (lane == 0) {
+    double* c = C + b * csb + i * csi + j * csj;
+    *c = alpha * acc + (beta != 0.0 ? beta * *c : 0.0);
+  }
+}
+
 struct Ctx {
   double* part;
   long long partsz;
@@ -90,6 +121,11 @@ cudaError_t contract(const Ctx& cx, const Opnd& A, const Opnd& B, double* C, lon
                      long long nk2, double alpha = 1.0, double beta = 0.0) {
   const long long nout = (long long)nb * ni * nj;
   if (nout == 0) return cudaSuccess;
+  if (nk1 * nk2 >= 64 && nout <= (4LL << 20)) {
+    k_contract_warp<<<(unsigned)((nout * 32 + 255) / 256), 256, 0, cx.s>>>(A, B, C, csb, csi, csj, nb, ni, nj,
+                                                                          nk1, nk2, alpha, beta);
+    return cudaGetLastError();
+  }
   // few outputs: split the first contracted index so that enough threads run (each output is
   // an FP64 dot product; unsplit, a few thousand threads would run long serial chains)
   long long want = (2LL * 152 * 1024) / nout;
@@ -143,8 +179,9 @@ __global__ void __launch_bounds__(256) k_gemm_t(Opnd A, Opnd B, double* C, long 
   double acc64[4][4] = {};
   for (long long kt = kt0; kt < kt1; ++kt) {
     const long long k0 = kt * kGK;
+    const bool a_rows = (A.sx == 1);  // stage along the contiguous index
     for (int e = threadIdx.x; e < kGM * kGK; e += 256) {
-      const int r = e / kGK, kk = e % kGK;
+      const int r = a_rows ? e % kGM : e / kGK, kk = a_rows ? e / kGM : e % kGK;
       const int gi = i0 + r;
       const long long gk = k0 + kk;
       float v = 0.f;
@@ -158,8 +195,9 @@ __global__ void __launch_bounds__(256) k_gemm_t(Opnd A, Opnd B, double* C, long 
       }
       As[kk][r] = v;
     }
+    const bool b_k = (B.sk1 == 1 && B.sx != 1);
     for (int e = threadIdx.x; e < kGK * kGN; e += 256) {
-      const int kk = e / kGN, c = e % kGN;
+      const int kk = b_k ? e % kGK : e / kGN, c = b_k ? e / kGK : e % kGN;
       const int gj = j0 + c;
       const long long gk = k0 + kk;
       float v = 0.f;
@@ -474,11 +512,12 @@ __global__ void __launch_bounds__(kT) k_bw_eig(EigArgs ea, int max_sweeps, int p
   double* U = ea.U + off;
   double* lam = ea.lam + slot * ea.slotM + ea.offM[mode];
   const int mp = (m + 1) & ~1;  // padded to even; index m (if m odd) is a dummy
+  const int ld = mp + 1;        // odd row stride: column sweeps hit distinct banks
   const int tid = threadIdx.x;
   if (!polish) {
     for (int e = tid; e < mp * mp; e += kT) {
       int r = e / mp, c = e % mp;
-      sA[e] = (r < m && c < m) ? M[(long long)r * m + c] : 0.0;
+      sA[r * ld + c] = (r < m && c < m) ? M[(long long)r * m + c] : 0.0;
     }
     for (int e = tid; e < m * m; e += kT) U[e] = ((e / m) == (e % m)) ? 1.0 : 0.0;
   } else {
@@ -496,7 +535,7 @@ __global__ void __launch_bounds__(kT) k_bw_eig(EigArgs ea, int max_sweeps, int p
       double acc = 0.0;
       if (r < m && c < m)
         for (int a = 0; a < m; ++a) acc = fma(U[(long long)a * m + r], W[(long long)a * m + c], acc);
-      sA[e] = acc;
+      sA[r * ld + c] = acc;
     }
   }
   __syncthreads();
@@ -505,7 +544,7 @@ __global__ void __launch_bounds__(kT) k_bw_eig(EigArgs ea, int max_sweeps, int p
   __shared__ double floor_abs;
   if (tid == 0) {
     double mxd = 0.0;
-    for (int j = 0; j < m; ++j) mxd = fmax(mxd, fabs(sA[j * mp + j]));
+    for (int j = 0; j < m; ++j) mxd = fmax(mxd, fabs(sA[j * ld + j]));
     floor_abs = 1e-17 * mxd;
   }
   __syncthreads();
@@ -520,8 +559,8 @@ __global__ void __launch_bounds__(kT) k_bw_eig(EigArgs ea, int max_sweeps, int p
         const int q = (k2 == 0) ? 0 : ((k2 - 1 + rd) % (mp - 1)) + 1;
         double c = 1.0, s = 0.0;
         if (p < m && q < m) {
-          const double apq = sA[p * mp + q];
-          const double app = sA[p * mp + p], aqq = sA[q * mp + q];
+          const double apq = sA[p * ld + q];
+          const double app = sA[p * ld + p], aqq = sA[q * ld + q];
           if (fabs(apq) > 1e-15 * sqrt(fabs(app * aqq)) && fabs(apq) > floor_abs) {
             const double th = (aqq - app) / (2.0 * apq);
             double tt;
@@ -545,9 +584,9 @@ __global__ void __launch_bounds__(kT) k_bw_eig(EigArgs ea, int max_sweeps, int p
         if (s == 0.0) continue;
         const int p = pp[t], q = qq[t];
         const double c = cs[t];
-        const double ap = sA[p * mp + col], aq = sA[q * mp + col];
-        sA[p * mp + col] = c * ap - s * aq;
-        sA[q * mp + col] = s * ap + c * aq;
+        const double ap = sA[p * ld + col], aq = sA[q * ld + col];
+        sA[p * ld + col] = c * ap - s * aq;
+        sA[q * ld + col] = s * ap + c * aq;
       }
       __syncthreads();
       // columns: A <- A G, U <- U G
@@ -557,9 +596,9 @@ __global__ void __launch_bounds__(kT) k_bw_eig(EigArgs ea, int max_sweeps, int p
         if (s == 0.0) continue;
         const int p = pp[t], q = qq[t];
         const double c = cs[t];
-        const double ap = sA[row * mp + p], aq = sA[row * mp + q];
-        sA[row * mp + p] = c * ap - s * aq;
-        sA[row * mp + q] = s * ap + c * aq;
+        const double ap = sA[row * ld + p], aq = sA[row * ld + q];
+        sA[row * ld + p] = c * ap - s * aq;
+        sA[row * ld + q] = s * ap + c * aq;
         if (row < m && p < m && q < m) {
           const double up = U[(long long)row * m + p], uq = U[(long long)row * m + q];
           U[(long long)row * m + p] = c * up - s * uq;
@@ -577,10 +616,10 @@ __global__ void __launch_bounds__(kT) k_bw_eig(EigArgs ea, int max_sweeps, int p
     for (int j = 0; j < m; ++j) {
       int best = j;
       for (int l = j + 1; l < m; ++l)
-        if (sA[perm[l] * mp + perm[l]] > sA[perm[best] * mp + perm[best]]) best = l;
+        if (sA[perm[l] * ld + perm[l]] > sA[perm[best] * ld + perm[best]]) best = l;
       int t = perm[j]; perm[j] = perm[best]; perm[best] = t;
     }
-    for (int j = 0; j < m; ++j) lam[j] = sA[perm[j] * mp + perm[j]];
+    for (int j = 0; j < m; ++j) lam[j] = sA[perm[j] * ld + perm[j]];
   }
   __syncthreads();
   for (int e = tid; e < m * m; e += kT) sA[e] = U[(long long)(e / m) * m + perm[e % m]];
@@ -606,18 +645,19 @@ __global__ void __launch_bounds__(kT) k_bw_eig32(EigArgs ea, int max_sweeps) {
   double* Uout = ea.U + off;
   double* lam = ea.lam + slot * ea.slotM + ea.offM[mode];
   const int mp = (m + 1) & ~1;
+  const int ld = mp + 1;  // odd row stride: column sweeps hit distinct banks
   float* sA = sF;
-  float* sU = sF + mp * mp;
+  float* sU = sF + mp * ld;
   const int tid = threadIdx.x;
   for (int e = tid; e < mp * mp; e += kT) {
     int r = e / mp, c = e % mp;
-    sA[e] = (r < m && c < m) ? (float)M[(long long)r * m + c] : 0.f;
-    sU[e] = (r == c) ? 1.f : 0.f;
+    sA[r * ld + c] = (r < m && c < m) ? (float)M[(long long)r * m + c] : 0.f;
+    sU[r * ld + c] = (r == c) ? 1.f : 0.f;
   }
   __syncthreads();
   if (tid == 0) {
     float mxd = 0.f;
-    for (int j = 0; j < m; ++j) mxd = fmaxf(mxd, fabsf(sA[j * mp + j]));
+    for (int j = 0; j < m; ++j) mxd = fmaxf(mxd, fabsf(sA[j * ld + j]));
     floor_abs = 1e-8f * mxd;
   }
   __syncthreads();
@@ -632,8 +672,8 @@ __global__ void __launch_bounds__(kT) k_bw_eig32(EigArgs ea, int max_sweeps) {
         const int q = (k2 == 0) ? 0 : ((k2 - 1 + rd) % (mp - 1)) + 1;
         float c = 1.f, s = 0.f;
         if (p < m && q < m) {
-          const float apq = sA[p * mp + q];
-          const float app = sA[p * mp + p], aqq = sA[q * mp + q];
+          const float apq = sA[p * ld + q];
+          const float app = sA[p * ld + p], aqq = sA[q * ld + q];
           if (fabsf(apq) > 1e-7f * sqrtf(fabsf(app * aqq)) && fabsf(apq) > floor_abs) {
             const float th = (aqq - app) / (2.f * apq);
             float tt;
@@ -656,9 +696,9 @@ __global__ void __launch_bounds__(kT) k_bw_eig32(EigArgs ea, int max_sweeps) {
         if (s == 0.f) continue;
         const int p = pp[t], q = qq[t];
         const float c = cs[t];
-        const float ap = sA[p * mp + col], aq = sA[q * mp + col];
-        sA[p * mp + col] = c * ap - s * aq;
-        sA[q * mp + col] = s * ap + c * aq;
+        const float ap = sA[p * ld + col], aq = sA[q * ld + col];
+        sA[p * ld + col] = c * ap - s * aq;
+        sA[q * ld + col] = s * ap + c * aq;
       }
       __syncthreads();
       for (int e = tid; e < (mp / 2) * mp; e += kT) {
@@ -667,12 +707,12 @@ __global__ void __launch_bounds__(kT) k_bw_eig32(EigArgs ea, int max_sweeps) {
         if (s == 0.f) continue;
         const int p = pp[t], q = qq[t];
         const float c = cs[t];
-        const float ap = sA[row * mp + p], aq = sA[row * mp + q];
-        sA[row * mp + p] = c * ap - s * aq;
-        sA[row * mp + q] = s * ap + c * aq;
-        const float up = sU[row * mp + p], uq = sU[row * mp + q];
-        sU[row * mp + p] = c * up - s * uq;
-        sU[row * mp + q] = s * up + c * uq;
+        const float ap = sA[row * ld + p], aq = sA[row * ld + q];
+        sA[row * ld + p] = c * ap - s * aq;
+        sA[row * ld + q] = s * ap + c * aq;
+        const float up = sU[row * ld + p], uq = sU[row * ld + q];
+        sU[row * ld + p] = c * up - s * uq;
+        sU[row * ld + q] = s * up + c * uq;
       }
       __syncthreads();
     }
@@ -684,13 +724,13 @@ __global__ void __launch_bounds__(kT) k_bw_eig32(EigArgs ea, int max_sweeps) {
     for (int j = 0; j < m; ++j) {
       int best = j;
       for (int l = j + 1; l < m; ++l)
-        if (sA[perm[l] * mp + perm[l]] > sA[perm[best] * mp + perm[best]]) best = l;
+        if (sA[perm[l] * ld + perm[l]] > sA[perm[best] * ld + perm[best]]) best = l;
       int t = perm[j]; perm[j] = perm[best]; perm[best] = t;
     }
-    for (int j = 0; j < m; ++j) lam[j] = (double)sA[perm[j] * mp + perm[j]];
+    for (int j = 0; j < m; ++j) lam[j] = (double)sA[perm[j] * ld + perm[j]];
   }
   __syncthreads();
-  for (int e = tid; e < m * m; e += kT) Uout[e] = (double)sU[(e / m) * mp + perm[e % m]];
+  for (int e = tid; e < m * m; e += kT) Uout[e] = (double)sU[(e / m) * ld + perm[e % m]];
 }
 
 inline unsigned nblk(long long n) { return (unsigned)((n + kT - 1) / kT); }
@@ -705,7 +745,7 @@ inline unsigned nblk(long long n) { return (unsigned)((n + kT - 1) / kT); }
 
 size_t backward_eig_smem(int m) {
   const int mp = (m + 1) & ~1;
-  return sizeof(double) * (size_t)mp * mp;
+  return sizeof(double) * (size_t)mp * (mp + 1);  // FP64: one padded panel; FP32: two
 }
 
 cudaError_t prepare_backward(int max_m) {
