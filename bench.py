@@ -414,12 +414,16 @@ def run_ours(a, rank, world):
                                "note": "same CUR iterates as the FP32 form; only S differs, near the threshold"}
         forms_out["fp32_fused"] = {"iters_per_s": value / world, "ms_per_iter": ms / K,
                                    "dense_ms": roof["ms_per_launch"] if roof else None}
-    # --- time to tolerance: whole solve from X resident, one graph launch ---
-    ev0.record(stream)
-    res = rt.rtcur_solve(plan, X.data_ptr(), idx, L.data_ptr(), S.data_ptr(), sh, max_iter=max_iter)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    ttt_ms = ev0.elapsed_time(ev1)
+    # --- time to tolerance: whole solve from X resident, one graph launch; median of 5 after 2 ---
+    ttts = []
+    for rep in range(7):
+        ev0.record(stream)
+        res = rt.rtcur_solve(plan, X.data_ptr(), idx, L.data_ptr(), S.data_ptr(), sh, max_iter=max_iter)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if rep >= 2:
+            ttts.append(ev0.elapsed_time(ev1))
+    ttt_ms = float(np.median(ttts))
     # --- end to end through the C ABI from pinned host buffers ---
     Xh = torch.from_numpy(p.X).pin_memory()
     Lh = torch.empty_like(Xh).pin_memory()
@@ -446,8 +450,8 @@ def run_ours(a, rank, world):
                    "dense_form": "fp32 fused (FMA last-mode product)", "pinv": "fp64",
                    "l2": f"inputs larger than L2 (X is {p.X.nbytes / 1e9:.2f} GB, L2 0.13 GB), no flush",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "time_to_tol": {"ms": ttt_ms, "iters": res.iters, "e": res.e, "status": res.status,
-                        "warm_hits": res.warm_hits,
+        "time_to_tol": {"ms": ttt_ms, "runs_ms": ttts, "iters": res.iters, "e": res.e, "status": res.status,
+                        "warm_hits": res.warm_hits, "statistic": "median of 5 solves after 2 warm-up solves",
                         "includes": "index upload, max|X|, the graph-driven loop, L and S output"},
         "e2e": {"value": e2e_val, "unit": "iters/s", "seconds": e2e_s, "iters": res_e2e.iters,
                 "h2d_bytes_per_step": int(p.X.nbytes), "d2h_bytes_per_step": int(p.X.nbytes),
