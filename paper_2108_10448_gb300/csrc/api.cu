@@ -598,6 +598,10 @@ rtcur_status rtcur_finish(rtcur_plan* p, float* L_out, float* S_out, rtcur_resul
   State h;
   CKC(p, cudaMemcpyAsync(&h, b.st, sizeof h, cudaMemcpyDeviceToHost, s));
   CKC(p, cudaStreamSynchronize(s));
+  if (full && S_out && h.k == 0) {  // no dense pass ran: S^(0) = 0
+    CKC(p, cudaMemsetAsync(S_out, 0, sizeof(float) * g.N, s));
+    CKC(p, cudaStreamSynchronize(s));
+  }
   int nh = h.k < g.max_iter ? h.k : g.max_iter;
   if (res) {
     if (res->e_hist && nh) CKC(p, cudaMemcpy(res->e_hist, b.e_hist, sizeof(double) * nh, cudaMemcpyDeviceToHost));
