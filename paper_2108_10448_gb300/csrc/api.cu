@@ -49,7 +49,6 @@ struct rtcur_plan {
   cudaGraph_t loopG = nullptr, iterG = nullptr;
   cudaGraphExec_t loopX = nullptr, iterX = nullptr;
   BwWork bw;             // adjoint workspace (options.checkpoint > 0)
-  alignas(64) unsigned char tmap_host[256];  // host copy of the TMA maps (tensor-core forms)
   std::vector<void*> allocs;
   std::vector<int> pos_host;
   std::string err;
@@ -352,7 +351,7 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
     g.sumDM = oDM;
   }
   if (o.scope == RTCUR_SCOPE_FULL && !dense_form_supported(g, o.dense_form))
-    return fail(nullptr, RTCUR_EINVAL, "dense_form %d does not support these dims/ranks (plain: 3 modes; BF16: d_n %% 8 == 0, d_n <= 1024, r_n <= 5; TF32: r_n <= 8)", o.dense_form);
+    return fail(nullptr, RTCUR_EINVAL, "dense_form %d does not support these dims/ranks (plain: 3 modes; BF16/TF32: d_n %% 4 == 0, d_n <= 1024; BF16: r_n <= 5; TF32: r_n <= 8)", o.dense_form);
   {
     long long oD = 0, oW = 0;
     for (int i = 0; i < n_modes; ++i) {
@@ -440,8 +439,6 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
   AL(b.tl_n, 1);
 #endif
   if (o.scope == RTCUR_SCOPE_FULL) AL(p->S_internal, g.N);
-  if (o.scope == RTCUR_SCOPE_FULL && (o.dense_form == RTCUR_FORM_BF16 || o.dense_form == RTCUR_FORM_TF32))
-    AL(b.tmap, 256);
   if (o.scope == RTCUR_SCOPE_FULL && o.dense_form == RTCUR_FORM_FP32_PLAIN) {
     AL(b.Ap[0], g.sumDM);
     AL(b.Ap[1], g.sumDM);
@@ -550,12 +547,7 @@ rtcur_status rtcur_begin(rtcur_plan* p, const float* X, const int64_t* idx, floa
   sp.X = X;
   sp.S = S;
   CKC(p, cudaMemcpyAsync(b.sp, &sp, sizeof sp, cudaMemcpyHostToDevice, s));
-  if (b.tmap) {  // TMA maps of this solve's X and S for the tensor-core forms
-    if (!S) return fail(p, RTCUR_EINVAL, "the tensor-core forms need an S buffer");
-    if (encode_umma_maps(g, X, S, p->tmap_host) != cudaSuccess)
-      return fail(p, RTCUR_ECUDA, "encoding the TMA maps of X and S failed");
-    CKC(p, cudaMemcpyAsync(b.tmap, p->tmap_host, 256, cudaMemcpyHostToDevice, s));
-  }
+
   CKC(p, cudaMemsetAsync(b.T[0], 0, sizeof(float) * g.rowsT * g.rlast, s));
   CKC(p, cudaMemsetAsync(b.B[0], 0, sizeof(float) * g.sumB, s));
   CKC(p, cudaMemsetAsync(b.G[0], 0, sizeof(float) * g.nG, s));

@@ -3,49 +3,46 @@
 // with the last mode product L = T B_n^T (T = G x_1 B_1 ... x_{n-1} B_{n-1}, Eq. (L=CUR) in
 // Tucker form) computed by tcgen05.mma into tensor memory.
 //
-// Work unit: a tile of 128 rows of X (rows of d_n contiguous floats) by 64 columns. Each CTA
-// (one per SM, persistent) takes a contiguous range of tiles, row tile outer, and runs three
-// warp roles:
-//   * producer warp: streams X tiles into a 5-stage shared-memory ring with 2-D TMA loads (two
-//     128 x 32 boxes per tile, 128-byte swizzle) completed on mbarriers;
-//   * MMA warp: writes the A operand (the tile's 128 rows of T, K-major, rebuilt when the row tile
-//     changes, double-buffered) and issues one tcgen05.mma (M = 128, N = 64) per tile into one of
-//     two 64-column TMEM accumulators, committed to an mbarrier; B (all of B_n, K-major, one
-//     64-row block per column block) is built once per launch;
-//   * two epilogue warpgroups on alternating tiles, each with its own accumulator: tcgen05.ld
-//     (warp w owns TMEM lanes 32(w%4).., i.e. tile rows, one row per thread), X from the
-//     swizzled stage (the 128-byte swizzle makes one row per thread conflict-free), threshold, S
-//     written in place and stored back with 2-D TMA stores; a stage is released when its store
-//     has read it, one tile of the warpgroup later, so stores overlap the next tiles. The
-//     residual / nnz / band sums are fused in.
+// The product is taken transposed: for a tile of 16 whole rows of X and a block of 128 columns,
+// D = B_n(block, :) T(tile rows, :)^T is one MMA with M = 128 (columns of X: TMEM lanes) and
+// N = 16 (rows of X: TMEM columns). X therefore moves in whole rows, as contiguous 1-D bulk copies
+// in both directions, and the epilogue reads it with one column per thread: consecutive threads
+// touch consecutive floats of shared memory, conflict-free without a swizzle.
+// Warp roles in each CTA (one per SM, persistent, a contiguous range of tiles):
+//   * producer warp: 1-D bulk loads of half tiles (8 rows) into a shared-memory ring (mbarriers);
+//   * MMA warp: the tile's 16 rows of T as the B operand (K-major, double-buffered) and one
+//     tcgen05.mma per 128-column block into a per-tile TMEM accumulator (two tiles in flight);
+//     B_n is the A operand, staged once per launch, one 128-row block per column block;
+//   * two epilogue warpgroups, warpgroup h on rows 8h..8h+7 of every tile: tcgen05.ld of its 8
+//     accumulator columns per block (warp w reads TMEM lanes 32(w%4)..: 32 columns of X), X from
+//     its half stage, threshold, S written in place; the half tile leaves in one 1-D bulk store and
+//     its stage is refilled once that store has read it. The residual / nnz / band sums are fused.
 // Forms (FP32 accumulation in both):
 //   BF16: kind::f16 with BF16 operands split x = hi + lo, the three significant products
-//         T_hi B_hi + T_hi B_lo + T_lo B_hi packed along K = 16 (3 r_n <= 15); the dropped
-//         T_lo B_lo term is ~2^-16 relative.
+//         B_hi T_hi + B_hi T_lo + B_lo T_hi packed along K = 16 (3 r_n <= 15); the dropped lo*lo
+//         term is ~2^-16 relative.
 //   TF32: kind::tf32, K = 8 >= r_n, operands rounded to TF32 (10-bit mantissa).
 // Every mbarrier wait is bounded; on expiry the kernel records RTCUR_ETIMEOUT, waits (bounded) for
-// its own copies and MMA in flight, frees its tensor memory and returns.
-#include <cuda.h>
+// its own copies and MMAs in flight, frees its tensor memory and returns.
 #include <cuda_bf16.h>
-#include <cudaTypedefs.h>
 
 #include "rtcur_internal.cuh"
 
 namespace {
 
-constexpr int kUEpiWarps = 8;        // warps 0-7: epilogue (two warpgroups on alternating tiles)
-constexpr int kUThreads = 32 * (kUEpiWarps + 2);  // + warp 8: TMA producer, warp 9: MMA
-constexpr int kURows = 128;          // M of the MMA, rows per tile
-constexpr int kUCols = 64;           // N of the MMA, columns per tile
-constexpr int kUBox = 32;            // columns per TMA box (128 bytes: the swizzle span)
-constexpr int kUStages = 5;
-constexpr int kUStageBytes = kURows * kUCols * 4;  // 32 KB
-constexpr int kUBoxBytes = kURows * kUBox * 4;     // 16 KB
-constexpr int kUOpBytes = kURows * 32;             // A: 128 rows x 32 bytes of K
-constexpr int kUOpBytesB = kUCols * 32;            // B: 64 rows x 32 bytes of K per column block
-constexpr int kUMaxCb = 16;                        // column blocks held in shared memory (d_n <= 1024)
+constexpr int kUEpiWarps = 8;                      // warps 0-7: epilogue (two warpgroups)
+constexpr int kUThreads = 32 * (kUEpiWarps + 2);   // + warp 8: bulk-copy producer, warp 9: MMA
+constexpr int kURows = 16;                         // rows per tile (N of the MMA)
+constexpr int kUHalf = kURows / 2;                 // rows per ring stage (one warpgroup's half)
+constexpr int kUCols = 128;                        // columns per block (M of the MMA)
+constexpr int kUMaxStages = 8;
+constexpr int kUOpBytesA = kUCols * 32;            // A: 128 rows (columns of X) x 32 bytes of K
+constexpr int kUOpBytesB = kURows * 32;            // B: 16 rows of T x 32 bytes of K
+constexpr int kUMaxCb = 8;                         // column blocks (d_n <= 1024)
+constexpr int kUTmemCols = 2 * kUMaxCb * kURows;   // two tiles of up to 8 blocks x 16 columns
 constexpr long long kUSpin = 1LL << 26;
 constexpr int kUMaxRed = 1024;
+constexpr int kUSmemLimit = 226 * 1024;            // dynamic shared memory (static use below 1 KB)
 
 __device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -64,19 +61,6 @@ __device__ __forceinline__ bool mb_wait(unsigned bar, unsigned parity) {
     if (mb_try(bar, parity)) return true;
   return false;
 }
-// AND of a predicate over the 128 threads of an epilogue warpgroup (named barrier `id`): a
-// decision every thread of the warpgroup takes together.
-__device__ __forceinline__ bool wg_all(bool v, int id) {
-  unsigned out;
-  asm volatile(
-      "{\n\t.reg .pred pi, po;\n\tsetp.ne.u32 pi, %1, 0;\n\tbar.red.and.pred po, %2, 128, pi;\n\t"
-      "selp.u32 %0, 1, 0, po;\n\t}"
-      : "=r"(out)
-      : "r"(v ? 1u : 0u), "r"(id)
-      : "memory");
-  return out != 0;
-}
-
 // K-major, no-swizzle operand block: row m (0..127), byte b (0..31) of its K slice.
 __device__ __forceinline__ unsigned op_off(int m, int b) {
   return (unsigned)((m >> 3) * 256 + (b >> 4) * 128 + (m & 7) * 16 + (b & 15));
@@ -142,56 +126,6 @@ __device__ __forceinline__ void op_row(const float* v, int r, bool a_side, unsig
   }
 }
 
-__device__ __forceinline__ void ht4(float4 x, const unsigned* l, float zf, float band, bool valid_row,
-                                    int col0, long long dn, float4& s, float& res, unsigned& nnz,
-                                    unsigned& inb) {
-  const float xs[4] = {x.x, x.y, x.z, x.w};
-  float ss[4];
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    const float dl = xs[e] - __uint_as_float(l[e]);
-    const float ad = fabsf(dl);
-    const bool keep = ad > zf;
-    ss[e] = keep ? dl : 0.f;
-    if (valid_row && col0 + e < dn) {
-      res = keep ? res : fmaf(dl, dl, res);
-      nnz += keep ? 1u : 0u;
-      inb += (fabsf(ad - zf) <= band) ? 1u : 0u;
-    }
-  }
-  s = make_float4(ss[0], ss[1], ss[2], ss[3]);
-}
-
-// Same without the bounds test: every element of an interior tile is in the tensor.
-__device__ __forceinline__ void ht4_full(float4 x, const unsigned* l, float zf, float band, float4& s,
-                                         float& res, unsigned& nnz, unsigned& inb) {
-  const float xs[4] = {x.x, x.y, x.z, x.w};
-  float ss[4];
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    const float dl = xs[e] - __uint_as_float(l[e]);
-    const float ad = fabsf(dl);
-    const bool keep = ad > zf;
-    ss[e] = keep ? dl : 0.f;
-    res = keep ? res : fmaf(dl, dl, res);
-    nnz += keep ? 1u : 0u;
-    inb += (fabsf(ad - zf) <= band) ? 1u : 0u;
-  }
-  s = make_float4(ss[0], ss[1], ss[2], ss[3]);
-}
-
-// 32 consecutive accumulator columns of this thread's TMEM lane (32x32b shape, x32)
-__device__ __forceinline__ void tmem_ld32(unsigned taddr, unsigned* l) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(l[0]), "=r"(l[1]), "=r"(l[2]), "=r"(l[3]), "=r"(l[4]), "=r"(l[5]), "=r"(l[6]), "=r"(l[7]),
-        "=r"(l[8]), "=r"(l[9]), "=r"(l[10]), "=r"(l[11]), "=r"(l[12]), "=r"(l[13]), "=r"(l[14]), "=r"(l[15]),
-        "=r"(l[16]), "=r"(l[17]), "=r"(l[18]), "=r"(l[19]), "=r"(l[20]), "=r"(l[21]), "=r"(l[22]), "=r"(l[23]),
-        "=r"(l[24]), "=r"(l[25]), "=r"(l[26]), "=r"(l[27]), "=r"(l[28]), "=r"(l[29]), "=r"(l[30]), "=r"(l[31])
-      : "r"(taddr));
-}
-
 __device__ __forceinline__ double block_sum_u(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -205,74 +139,69 @@ __device__ __forceinline__ double block_sum_u(double v, double* sh) {
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(kUThreads, 1) k_dense_umma(Geom g, Bufs b) {
-  extern __shared__ unsigned char dsm_raw[];
-  __shared__ unsigned long long xfull[kUStages], xempty[kUStages], tfull[2], tempty[2];
+__global__ void __launch_bounds__(kUThreads, 1) k_dense_umma(Geom g, Bufs b, int nstages) {
+  extern __shared__ __align__(128) unsigned char dsm[];
+  __shared__ unsigned long long xfull[kUMaxStages], xempty[kUMaxStages], tfull[2], tempty[2];
   __shared__ unsigned tbase;
-  __shared__ volatile int ep_abort, prod_abort, mma_abort;  // each written by one thread only
-  __shared__ int n_issued[kUStages], n_seen[kUStages], n_mma[2], n_mma_seen[2];
+  __shared__ volatile int ep_abort, prod_abort, mma_abort;  // set to 1 only
+  __shared__ int n_issued[kUMaxStages], n_mma[2];
   __shared__ double sh[kUThreads / 32];
   TL_BEGIN();
-  // 1024-byte aligned base (the 128-byte swizzle atoms of TMA need it)
-  const unsigned raw = su32(dsm_raw);
-  unsigned char* dsm = dsm_raw + (((raw + 1023u) & ~1023u) - raw);
-  unsigned char* stage0 = dsm;                               // kUStages x 32 KB
-  unsigned char* bop = dsm + kUStages * kUStageBytes;        // ncb x 2 KB
   const State* st = b.st;
   const int cur = st->k & 1;
   const double zeta = g.gamma * st->zeta;
   const float zf = (float)zeta;
   const float band = (float)(g.inband * zeta);
+  const float* __restrict__ X = b.sp->X;
+  float* __restrict__ S = b.sp->S;
   const float* __restrict__ T = b.T[cur];
   const float* __restrict__ Bn = b.B[cur] + g.offB[g.n - 1];
   const int rn = g.rlast;
-  const long long dn = g.d[g.n - 1];
+  const int dn = (int)g.d[g.n - 1];
   const long long rows = g.rowsT;
-  const int ncb = (int)((dn + kUCols - 1) / kUCols);
-  unsigned char* aop = bop + ncb * kUOpBytesB;               // 2 x 4 KB
-  const long long nrt = (rows + kURows - 1) / kURows;
-  const long long U = nrt * ncb;
-  const long long u0 = U * blockIdx.x / gridDim.x, u1 = U * (blockIdx.x + 1) / gridDim.x;
+  const int ncb = (dn + kUCols - 1) / kUCols;
+  const int stage_f = kUHalf * dn;                              // floats per ring stage
+  float* ring = reinterpret_cast<float*>(dsm);
+  unsigned char* aop = dsm + (size_t)nstages * stage_f * 4;     // ncb x 4 KB (B_n blocks)
+  unsigned char* bop = aop + ncb * kUOpBytesA;                  // 2 x 512 B (T rows of a tile)
+  const long long ntiles = (rows + kURows - 1) / kURows;
+  const long long u0 = ntiles * blockIdx.x / gridDim.x, u1 = ntiles * (blockIdx.x + 1) / gridDim.x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const unsigned long long mapX = reinterpret_cast<unsigned long long>(b.tmap);
-  const unsigned long long mapS = mapX + 128;
 
-  // B operand: row n of column block cb is B_n(cb*64 + n, :) (zero beyond d_n)
+  // A operand: row m of column block cb is B_n(cb * 128 + m, :) (zero beyond d_n)
   for (int e = tid; e < ncb * kUCols; e += kUThreads) {
-    const int cb = e / kUCols, n = e % kUCols;
-    const long long col = (long long)cb * kUCols + n;
+    const int cb = e / kUCols, m = e % kUCols;
+    const int col = cb * kUCols + m;
     float v[8];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) v[c] = (col < dn && c < rn) ? __ldg(Bn + col * rn + c) : 0.f;
+    for (int c = 0; c < 8; ++c) v[c] = (col < dn && c < rn) ? __ldg(Bn + (size_t)col * rn + c) : 0.f;
     unsigned w[8];
-    op_row<KIND>(v, rn, false, w);
-    unsigned char* blk = bop + cb * kUOpBytesB;
-    *reinterpret_cast<uint4*>(blk + op_off(n, 0)) = make_uint4(w[0], w[1], w[2], w[3]);
-    *reinterpret_cast<uint4*>(blk + op_off(n, 16)) = make_uint4(w[4], w[5], w[6], w[7]);
+    op_row<KIND>(v, rn, true, w);
+    unsigned char* blk = aop + cb * kUOpBytesA;
+    *reinterpret_cast<uint4*>(blk + op_off(m, 0)) = make_uint4(w[0], w[1], w[2], w[3]);
+    *reinterpret_cast<uint4*>(blk + op_off(m, 16)) = make_uint4(w[4], w[5], w[6], w[7]);
   }
   if (tid == 0) {
     ep_abort = prod_abort = mma_abort = 0;
-    for (int s = 0; s < kUStages; ++s) {
-      n_issued[s] = n_seen[s] = 0;
+    for (int s = 0; s < kUMaxStages; ++s) {
+      n_issued[s] = 0;
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&xfull[s])) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&xempty[s])) : "memory");
     }
     for (int a = 0; a < 2; ++a) {
-      n_mma[a] = n_mma_seen[a] = 0;
+      n_mma[a] = 0;
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&tfull[a])) : "memory");
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&tempty[a])), "r"(kUEpiWarps / 2) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&tempty[a])), "r"(kUEpiWarps) : "memory");
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    // the maps were written by host copies: order them before the TMA proxy reads them
-    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(mapX) : "memory");
-    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(mapS) : "memory");
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(su32(&tbase))
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tbase)),
+                 "r"(kUTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // B operand -> async proxy
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // A operand -> async proxy
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -282,41 +211,44 @@ __global__ void __launch_bounds__(kUThreads, 1) k_dense_umma(Geom g, Bufs b) {
   unsigned nnz = 0u, inb = 0u;
 
   if (warp == kUEpiWarps) {
-    // ---------------- producer: TMA loads of X tiles into the stage ring
+    // ---------------- producer: 1-D bulk loads of half tiles j = 2 (u - u0) + h, in order
     if (lane == 0) {
-      for (long long u = u0; u < u1; ++u) {
-        const int i = (int)(u - u0), s = i % kUStages;
+      const long long nj = 2 * (u1 - u0);
+      for (long long j = 0; j < nj; ++j) {
+        const int s = (int)(j % nstages);
         if (ep_abort || mma_abort) break;
-        if (i >= kUStages && !mb_wait(su32(&xempty[s]), (unsigned)(((i / kUStages) - 1) & 1))) {
+        if (j >= nstages && !mb_wait(su32(&xempty[s]), (unsigned)(((j / nstages) - 1) & 1))) {
           prod_abort = 1;
           break;
         }
-        const long long rt = u / ncb;
-        const int cb = (int)(u % ncb);
-        const int c0 = cb * kUCols;
-        int nbox = (int)((dn - c0 + kUBox - 1) / kUBox);
-        if (nbox > kUCols / kUBox) nbox = kUCols / kUBox;
+        const long long r0 = (u0 + (j >> 1)) * kURows + (j & 1) * kUHalf;
+        const long long nr = r0 >= rows ? 0 : (r0 + kUHalf <= rows ? kUHalf : rows - r0);
         const unsigned bar = su32(&xfull[s]);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                     "r"((unsigned)(nbox * kUBoxBytes))
-                     : "memory");
-        for (int j = 0; j < nbox; ++j) {
-          const unsigned dst = su32(stage0 + s * kUStageBytes + j * kUBoxBytes);
+        if (nr == 0) {  // empty second half of a ragged last tile: complete the phase
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+        } else {
+          const unsigned bytes = (unsigned)(nr * dn * 4);
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
           asm volatile(
-              "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-                  dst),
-              "l"(mapX), "r"(c0 + j * kUBox), "r"((int)(rt * kURows)), "r"(bar)
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                  su32(ring + (size_t)s * stage_f)),
+              "l"(X + r0 * dn), "r"(bytes), "r"(bar)
               : "memory");
         }
         ++n_issued[s];
       }
     }
   } else if (warp == kUEpiWarps + 1) {
-    // ---------------- MMA warp: A operand (the tile's rows of T) and one MMA per tile
-    long long prev_rt = -1;
-    int abuf = 1;
+    // ---------------- MMA warp: B operand (the tile's 16 rows of T), one MMA per column block
+    const unsigned idesc = (1u << 4) | ((KIND == 1 ? 2u : 1u) << 7) | ((KIND == 1 ? 2u : 1u) << 10) |
+                           ((unsigned)(kURows >> 3) << 17) | ((unsigned)(kUCols >> 4) << 24);
     for (long long u = u0; u < u1; ++u) {
       const int i = (int)(u - u0), a = i & 1;
+      // this tile's rows of T, loaded before the wait so their latency overlaps it
+      const long long grow = u * kURows + (lane & (kURows - 1));
+      float v[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) v[c] = (grow < rows && c < rn) ? __ldg(T + grow * rn + c) : 0.f;
       int stop = 0;  // decided by lane 0, broadcast: the warp leaves the loop together
       if (lane == 0) {
         const bool ok = (i < 2) || mb_wait(su32(&tempty[a]), (unsigned)(((i >> 1) - 1) & 1));
@@ -325,43 +257,33 @@ __global__ void __launch_bounds__(kUThreads, 1) k_dense_umma(Geom g, Bufs b) {
       }
       if (__shfl_sync(0xffffffffu, stop, 0)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const long long rt = u / ncb;
-      const int cb = (int)(u % ncb);
-      if (rt != prev_rt) {  // every MMA that read this A buffer has completed (see tempty)
-        abuf ^= 1;
-        unsigned char* ab = aop + abuf * kUOpBytes;
-        for (int r = lane; r < kURows; r += 32) {
-          const long long grow = rt * kURows + r;
-          float v[8];
-#pragma unroll
-          for (int c = 0; c < 8; ++c) v[c] = (grow < rows && c < rn) ? __ldg(T + grow * rn + c) : 0.f;
-          unsigned w[8];
-          op_row<KIND>(v, rn, true, w);
-          *reinterpret_cast<uint4*>(ab + op_off(r, 0)) = make_uint4(w[0], w[1], w[2], w[3]);
-          *reinterpret_cast<uint4*>(ab + op_off(r, 16)) = make_uint4(w[4], w[5], w[6], w[7]);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncwarp();
-        prev_rt = rt;
+      unsigned char* bb = bop + a * kUOpBytesB;
+      if (lane < kURows) {  // the MMAs that read this buffer (two tiles ago) have completed
+        unsigned w[8];
+        op_row<KIND>(v, rn, false, w);
+        *reinterpret_cast<uint4*>(bb + op_off(lane, 0)) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4*>(bb + op_off(lane, 16)) = make_uint4(w[4], w[5], w[6], w[7]);
       }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
       if (lane == 0) {
-        const unsigned long long ad = op_desc(su32(aop + abuf * kUOpBytes));
-        const unsigned long long bd = op_desc(su32(bop + cb * kUOpBytesB));
-        const unsigned idesc = (1u << 4) | ((KIND == 1 ? 2u : 1u) << 7) | ((KIND == 1 ? 2u : 1u) << 10) |
-                               ((unsigned)(kUCols >> 3) << 17) | ((unsigned)(kURows >> 4) << 24);
-        const unsigned dt = tmem + (unsigned)(a * kUCols);
-        if (KIND == 1)
-          asm volatile(
-              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-              "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
-              "l"(ad), "l"(bd), "r"(idesc), "r"(0)
-              : "memory");
-        else
-          asm volatile(
-              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
-              "l"(ad), "l"(bd), "r"(idesc), "r"(0)
-              : "memory");
+        const unsigned long long bd = op_desc(su32(bb));
+        for (int cb = 0; cb < ncb; ++cb) {
+          const unsigned long long ad = op_desc(su32(aop + cb * kUOpBytesA));
+          const unsigned dt = tmem + (unsigned)(a * (kUTmemCols / 2) + cb * kURows);
+          if (KIND == 1)
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(0)
+                : "memory");
+          else
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(0)
+                : "memory");
+        }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          su32(&tfull[a]))
                      : "memory");
@@ -370,77 +292,89 @@ __global__ void __launch_bounds__(kUThreads, 1) k_dense_umma(Geom g, Bufs b) {
       __syncwarp();
     }
   } else {
-    // ---------------- epilogue: two warpgroups on alternating tiles (warpgroup h takes the
-    // tiles i = h, h + 2, ... and accumulator h)
-    const int q = warp & 3;                // TMEM lane quarter of this warp
-    const int h = warp >> 2;               // warpgroup
-    const int r = q * 32 + lane;           // tile row == TMEM lane
-    const int et = tid & 127;              // thread within the warpgroup
-    const int bar_id = 1 + h;
-    for (long long u = u0 + h; u < u1; u += 2) {
-      const int i = (int)(u - u0), s = i % kUStages, a = h;
-      const long long rt = u / ncb;
-      const int cb = (int)(u % ncb);
-      const int c0 = cb * kUCols;
-      int nbox = (int)((dn - c0 + kUBox - 1) / kUBox);
-      if (nbox > kUCols / kUBox) nbox = kUCols / kUBox;
-      const long long grow = rt * kURows + r;
-      const bool vrow = grow < rows;
+    // ---------------- epilogue: warpgroup h on rows 8h..8h+7 of each tile (its half stage)
+    const int q = warp & 3;  // TMEM lane quarter: columns 32q.. of every block
+    const int h = warp >> 2;
+    const int et = tid & 127;
+    const int nq = (dn - q * 32 + kUCols - 1) / kUCols;  // blocks with columns in this quarter
+    for (long long u = u0; u < u1; ++u) {
+      const int i = (int)(u - u0), a = i & 1;
+      const long long j = 2 * (long long)i + h;
+      const int s = (int)(j % nstages);
+      const long long r0 = u * kURows + h * kUHalf;
+      const int nr = (int)(r0 >= rows ? 0 : (r0 + kUHalf <= rows ? kUHalf : rows - r0));
       const bool ok_t = mb_wait(su32(&tfull[a]), (unsigned)((i >> 1) & 1));
-      const bool ok_x = ok_t && mb_wait(su32(&xfull[s]), (unsigned)((i / kUStages) & 1));
-      if (!wg_all(ok_t && ok_x, bar_id)) {  // uniform within the warpgroup
-        if (et == 0) {
-          if (ok_t) ++n_mma_seen[a];
-          if (ok_x) ++n_seen[s];
-          ep_abort = 1;
-        }
+      const bool ok_x = ok_t && mb_wait(su32(&xfull[s]), (unsigned)((j / nstages) & 1));
+      unsigned allok;  // AND over the warpgroup (named barrier 1 + h): it leaves together
+      asm volatile(
+          "{\n\t.reg .pred pi, po;\n\tsetp.ne.u32 pi, %1, 0;\n\tbar.red.and.pred po, %2, 128, pi;\n\t"
+          "selp.u32 %0, 1, 0, po;\n\t}"
+          : "=r"(allok)
+          : "r"((ok_t && ok_x) ? 1u : 0u), "r"(1 + h)
+          : "memory");
+      if (!allok) {
+        if (et == 0) ep_abort = 1;
         break;
       }
-      if (et == 0) {
-        ++n_mma_seen[a];
-        ++n_seen[s];
-      }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      unsigned char* stg = stage0 + s * kUStageBytes;
-      // both 32-column halves of the accumulator, one wait
-      unsigned l[64];
-      const unsigned taddr = tmem + ((unsigned)(q * 32) << 16) + (unsigned)(a * kUCols);
-      tmem_ld32(taddr, l);
-      tmem_ld32(taddr + kUBox, l + 32);
+      // this warp's 8 accumulator columns of every block, one wait
+      unsigned l[kUMaxCb][kUHalf];
+      const unsigned tq = tmem + ((unsigned)(q * 32) << 16) + (unsigned)(a * (kUTmemCols / 2) + h * kUHalf);
+#pragma unroll
+      for (int cb = 0; cb < kUMaxCb; ++cb)
+        if (cb < nq)
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                       : "=r"(l[cb][0]), "=r"(l[cb][1]), "=r"(l[cb][2]), "=r"(l[cb][3]), "=r"(l[cb][4]),
+                         "=r"(l[cb][5]), "=r"(l[cb][6]), "=r"(l[cb][7])
+                       : "r"(tq + (unsigned)(cb * kURows)));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      const bool interior = (rt + 1) * kURows <= rows && c0 + kUCols <= dn;
-#pragma unroll
-      for (int j = 0; j < kUCols / kUBox; ++j) {
-        if (j >= nbox) break;
-        unsigned char* rowp = stg + j * kUBoxBytes + r * 128;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          float4* p = reinterpret_cast<float4*>(rowp + ((c ^ (r & 7)) << 4));
-          float4 sv;
-          if (interior)
-            ht4_full(*p, l + 32 * j + 4 * c, zf, band, sv, res, nnz, inb);
-          else
-            ht4(*p, l + 32 * j + 4 * c, zf, band, vrow, c0 + j * kUBox + 4 * c, dn, sv, res, nnz, inb);
-          *p = sv;
-        }
-      }
-      // this warp is done with accumulator a
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&tempty[a])) : "memory");
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // S tile -> TMA store
-      asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");
-      if (et == 0) {
-        for (int j = 0; j < nbox; ++j) {
-          const unsigned src = su32(stg + j * kUBoxBytes);
-          asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(mapS),
-                       "r"(c0 + j * kUBox), "r"((int)(rt * kURows)), "r"(src)
-                       : "memory");
+      float* stg = ring + (size_t)s * stage_f;
+#pragma unroll
+      for (int cb = 0; cb < kUMaxCb; ++cb) {
+        const int col = cb * kUCols + q * 32 + lane;
+        if (cb < nq && col < dn) {
+          float* p = stg + col;
+          if (nr == kUHalf) {
+#pragma unroll
+            for (int r = 0; r < kUHalf; ++r) {
+              const float dl = p[r * dn] - __uint_as_float(l[cb][r]);
+              const float ad = fabsf(dl);
+              const bool keep = ad > zf;
+              p[r * dn] = keep ? dl : 0.f;
+              res = keep ? res : fmaf(dl, dl, res);
+              nnz += keep ? 1u : 0u;
+              inb += (fabsf(ad - zf) <= band) ? 1u : 0u;
+            }
+          } else {
+#pragma unroll
+            for (int r = 0; r < kUHalf; ++r) {
+              if (r < nr) {
+                const float dl = p[r * dn] - __uint_as_float(l[cb][r]);
+                const float ad = fabsf(dl);
+                const bool keep = ad > zf;
+                p[r * dn] = keep ? dl : 0.f;
+                res = keep ? res : fmaf(dl, dl, res);
+                nnz += keep ? 1u : 0u;
+                inb += (fabsf(ad - zf) <= band) ? 1u : 0u;
+              }
+            }
+          }
         }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // S half tile -> bulk store
+      asm volatile("bar.sync %0, 128;" ::"r"(1 + h) : "memory");
+      if (et == 0) {
+        if (nr > 0)
+          asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(S + r0 * dn),
+                       "r"(su32(stg)), "r"((unsigned)(nr * dn * 4))
+                       : "memory");
         asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-        if (i >= 2) {  // this warpgroup's previous tile has been read by its store: release its stage
+        if (i >= 1) {  // this warpgroup's previous store has read its stage: release it
           asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
-          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&xempty[(i - 2) % kUStages]))
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&xempty[(j - 2) % nstages]))
                        : "memory");
         }
       }
@@ -449,19 +383,20 @@ __global__ void __launch_bounds__(kUThreads, 1) k_dense_umma(Geom g, Bufs b) {
   }
   __syncthreads();
   if ((ep_abort || prod_abort || mma_abort) && tid == 0) {
-    // drain: every TMA load and MMA this CTA issued completes before its shared and tensor
-    // memory are released (at most one unconsumed load per stage and one MMA per accumulator)
-    for (int s = 0; s < kUStages; ++s)
-      if (n_issued[s] > n_seen[s]) mb_wait(su32(&xfull[s]), (unsigned)((n_issued[s] - 1) & 1));
+    // drain: every bulk load and MMA this CTA issued completes before its shared and tensor
+    // memory are released (at most one outstanding per stage and per accumulator; waiting on a
+    // completed phase returns at once)
+    for (int s = 0; s < nstages; ++s)
+      if (n_issued[s] > 0) mb_wait(su32(&xfull[s]), (unsigned)((n_issued[s] - 1) & 1));
     for (int a = 0; a < 2; ++a)
-      if (n_mma[a] > n_mma_seen[a]) mb_wait(su32(&tfull[a]), (unsigned)((n_mma[a] - 1) & 1));
+      if (n_mma[a] > 0) mb_wait(su32(&tfull[a]), (unsigned)((n_mma[a] - 1) & 1));
     atomicExch(&b.st->err, -5);  // RTCUR_ETIMEOUT
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kUTmemCols) : "memory");
   }
   // reductions: residual, nnz, band count (the producer and MMA warps add zeros)
   double* part = b.red + (size_t)TK_DENSE * kUMaxRed * RT_RED_SLOTS;
@@ -488,28 +423,28 @@ __global__ void __launch_bounds__(kUThreads, 1) k_dense_umma(Geom g, Bufs b) {
   TL_END(1);
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
-  return fn;
-}
-
-}  // namespace
-
-size_t umma_smem(const Geom& g, int kind) {
+// Ring stages (8-row halves) that fit beside the operands; 0: the form does not apply.
+int umma_stages(const Geom& g, int kind) {
   const long long dn = g.d[g.n - 1];
   if (dn % 4 != 0 || dn > (long long)kUMaxCb * kUCols) return 0;
   if (kind == 0 ? (3 * g.rlast > 16) : (g.rlast > 8)) return 0;
   if (g.rowsT >= (1LL << 31)) return 0;
   const int ncb = (int)((dn + kUCols - 1) / kUCols);
-  return 1024 + (size_t)kUStages * kUStageBytes + (size_t)ncb * kUOpBytesB + 2 * (size_t)kUOpBytes;
+  const long long fixed = (long long)ncb * kUOpBytesA + 2 * kUOpBytesB;
+  const long long stage = (long long)kUHalf * dn * 4;
+  long long n = (kUSmemLimit - fixed) / stage;
+  if (n > kUMaxStages) n = kUMaxStages;
+  return n >= 3 ? (int)n : 0;  // three stages at least: a stage is released one half tile late
+}
+
+}  // namespace
+
+size_t umma_smem(const Geom& g, int kind) {
+  const int ns = umma_stages(g, kind);
+  if (!ns) return 0;
+  const long long dn = g.d[g.n - 1];
+  const int ncb = (int)((dn + kUCols - 1) / kUCols);
+  return (size_t)ns * kUHalf * dn * 4 + (size_t)ncb * kUOpBytesA + 2 * kUOpBytesB;
 }
 
 cudaError_t prepare_umma(const Geom& g, int kind) {
@@ -525,35 +460,13 @@ cudaError_t prepare_umma(const Geom& g, int kind) {
 cudaError_t launch_umma(const Geom& g, const Bufs& b, int kind, cudaStream_t s) {
   const size_t smem = umma_smem(g, kind);
   if (!smem) return cudaErrorNotSupported;
-  const long long dn = g.d[g.n - 1];
-  const long long units = ((g.rowsT + kURows - 1) / kURows) * ((dn + kUCols - 1) / kUCols);
+  const int ns = umma_stages(g, kind);
+  const long long ntiles = (g.rowsT + kURows - 1) / kURows;
   const int ctas = g.dense_ctas > 0 ? g.dense_ctas : 144;
-  const int grid = (int)(units < ctas ? units : ctas);
+  const int grid = (int)(ntiles < ctas ? ntiles : ctas);
   if (kind == 0)
-    k_dense_umma<0><<<grid, kUThreads, smem, s>>>(g, b);
+    k_dense_umma<0><<<grid, kUThreads, smem, s>>>(g, b, ns);
   else
-    k_dense_umma<1><<<grid, kUThreads, smem, s>>>(g, b);
+    k_dense_umma<1><<<grid, kUThreads, smem, s>>>(g, b, ns);
   return cudaGetLastError();
-}
-
-// Host-encoded TMA maps of X (read) and S (written), each the 2-D view rows x d_n of FP32 with
-// 128 x 32 boxes and the 128-byte swizzle, written into the 256 bytes at `dst_host` (copied to the
-// plan's device buffer by the caller).
-cudaError_t encode_umma_maps(const Geom& g, const float* X, float* S, void* dst_host) {
-  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
-  if (!enc) return cudaErrorNotSupported;
-  const long long dn = g.d[g.n - 1];
-  cuuint64_t gdim[2] = {(cuuint64_t)dn, (cuuint64_t)g.rowsT};
-  cuuint64_t gstride[1] = {(cuuint64_t)(dn * 4)};
-  cuuint32_t box[2] = {(cuuint32_t)kUBox, (cuuint32_t)kURows};
-  cuuint32_t estr[2] = {1, 1};
-  CUtensorMap* maps = static_cast<CUtensorMap*>(dst_host);
-  const float* ptrs[2] = {X, S};
-  for (int k = 0; k < 2; ++k) {
-    CUresult r = enc(&maps[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(ptrs[k]), gdim, gstride, box,
-                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-  }
-  return cudaSuccess;
 }

@@ -143,7 +143,6 @@ struct Bufs {
   float* Lplain;         // plain form: the materialised L^(k)
   TlRec* tl;             // diagnostic timeline (null unless built with -DRTCUR_TIMELINE)
   unsigned* tl_n;
-  unsigned char* tmap;   // tensor-core forms: TMA maps of X and S (2 x 128 bytes, device)
   float* ckV;            // ck_iters * nS: sampled values X - S of each recorded iteration
   unsigned char* ckM;    // ck_iters * nS: their HT masks (1 = thresholded, the value is L^(k))
 };
@@ -173,7 +172,6 @@ struct BwWork {
 size_t umma_smem(const Geom& g, int kind);  // 0 when the form does not apply
 cudaError_t prepare_umma(const Geom& g, int kind);
 cudaError_t launch_umma(const Geom& g, const Bufs& b, int kind, cudaStream_t s);
-cudaError_t encode_umma_maps(const Geom& g, const float* X, float* S, void* dst_host);
 
 void backward_layout(const Geom& g, BwWork& w);
 cudaError_t prepare_backward(int max_m);
