@@ -8,7 +8,9 @@
 // N = 16 (rows of X: TMEM columns). X therefore moves in whole rows, as contiguous 1-D bulk copies
 // in both directions, and the epilogue reads it with one column per thread: consecutive threads
 // touch consecutive floats of shared memory, conflict-free without a swizzle.
-// Warp roles in each CTA (one per SM, persistent, a contiguous range of tiles):
+// One persistent CTA per SM; its footprint (80 registers a thread, at most 184 KB of shared
+// memory) leaves each SM room for a CTA of the sampled chain's refinement cluster, which runs
+// beside this pass in the same iteration. Warp roles (a contiguous range of tiles per CTA):
 //   * producer warp: 1-D bulk loads of half tiles (8 rows) into a shared-memory ring (mbarriers);
 //   * MMA warp: the tile's 16 rows of T as the B operand (K-major, double-buffered) and one
 //     tcgen05.mma per 128-column block into a per-tile TMEM accumulator (two tiles in flight);
@@ -39,10 +41,15 @@ constexpr int kUMaxStages = 8;
 constexpr int kUOpBytesA = kUCols * 32;            // A: 128 rows (columns of X) x 32 bytes of K
 constexpr int kUOpBytesB = kURows * 32;            // B: 16 rows of T x 32 bytes of K
 constexpr int kUMaxCb = 8;                         // column blocks (d_n <= 1024)
+constexpr int kUGroup = 4;                         // blocks read from TMEM per wait
 constexpr int kUTmemCols = 2 * kUMaxCb * kURows;   // two tiles of up to 8 blocks x 16 columns
 constexpr long long kUSpin = 1LL << 26;
 constexpr int kUMaxRed = 1024;
-constexpr int kUSmemLimit = 226 * 1024;            // dynamic shared memory (static use below 1 KB)
+// Room left on the SM for one CTA of the sampled chain's cluster kernel (256 threads x 128
+// registers, ~40 KB of shared memory), which runs beside this pass: registers are split among the
+// SM's four schedulers, three of this kernel's ten warps share one, so 80 registers a thread.
+constexpr int kUMaxRegs = 80;
+constexpr int kUSmemLimit = 184 * 1024;            // dynamic shared memory of this pass
 
 __device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -61,6 +68,25 @@ __device__ __forceinline__ bool mb_wait(unsigned bar, unsigned parity) {
     if (mb_try(bar, parity)) return true;
   return false;
 }
+// Named barriers of one epilogue warpgroup (128 threads). The id is an immediate: a barrier id in
+// a register makes the compiler reserve all 16 hardware barriers of the CTA, which keeps other
+// kernels' CTAs (the sampled chain's) off the SM.
+template <int ID>
+__device__ __forceinline__ bool wg_and(bool v) {
+  unsigned out;
+  asm volatile(
+      "{\n\t.reg .pred pi, po;\n\tsetp.ne.u32 pi, %1, 0;\n\tbar.red.and.pred po, %2, 128, pi;\n\t"
+      "selp.u32 %0, 1, 0, po;\n\t}"
+      : "=r"(out)
+      : "r"(v ? 1u : 0u), "n"(ID)
+      : "memory");
+  return out != 0;
+}
+template <int ID>
+__device__ __forceinline__ void wg_sync() {
+  asm volatile("bar.sync %0, 128;" ::"n"(ID) : "memory");
+}
+
 // K-major, no-swizzle operand block: row m (0..127), byte b (0..31) of its K slice.
 __device__ __forceinline__ unsigned op_off(int m, int b) {
   return (unsigned)((m >> 3) * 256 + (b >> 4) * 128 + (m & 7) * 16 + (b & 15));
@@ -126,6 +152,37 @@ __device__ __forceinline__ void op_row(const float* v, int r, bool a_side, unsig
   }
 }
 
+// One element of the epilogue: D = X - L in place of X (the stage), kept when |D| > zeta, with
+// the residual, kept-count and band-count sums.
+__device__ __forceinline__ void ht1(float* p, unsigned lbits, float zf, float band, float& res, unsigned& nnz,
+                                    unsigned& inb) {
+  const float dl = *p - __uint_as_float(lbits);
+  const float ad = fabsf(dl);
+  const bool keep = ad > zf;
+  *p = keep ? dl : 0.f;
+  res = keep ? res : fmaf(dl, dl, res);
+  nnz += keep ? 1u : 0u;
+  inb += (fabsf(ad - zf) <= band) ? 1u : 0u;
+}
+// A warp is done reading a TMEM accumulator: order its loads before the arrive on `bar`.
+__device__ __forceinline__ void release_acc(unsigned long long* bar, int lane) {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncwarp();
+  if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
+}
+
+// Starts the TMEM loads of blocks cb0 .. cb0 + kUGroup - 1 (those below nq): 8 accumulator columns
+// (rows of X) of this warp's 32 lanes (columns of X) each. Completed by tcgen05.wait::ld.
+__device__ __forceinline__ void tmem_group(unsigned tq, int cb0, int nq, unsigned (&l)[kUGroup][kUHalf]) {
+#pragma unroll
+  for (int c = 0; c < kUGroup; ++c)
+    if (cb0 + c < nq)
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                   : "=r"(l[c][0]), "=r"(l[c][1]), "=r"(l[c][2]), "=r"(l[c][3]), "=r"(l[c][4]), "=r"(l[c][5]),
+                     "=r"(l[c][6]), "=r"(l[c][7])
+                   : "r"(tq + (unsigned)((cb0 + c) * kURows)));
+}
+
 __device__ __forceinline__ double block_sum_u(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -139,7 +196,7 @@ __device__ __forceinline__ double block_sum_u(double v, double* sh) {
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(kUThreads, 1) k_dense_umma(Geom g, Bufs b, int nstages) {
+__global__ void __maxnreg__(kUMaxRegs) k_dense_umma(Geom g, Bufs b, int nstages) {
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ unsigned long long xfull[kUMaxStages], xempty[kUMaxStages], tfull[2], tempty[2];
   __shared__ unsigned tbase;
@@ -305,67 +362,48 @@ __global__ void __launch_bounds__(kUThreads, 1) k_dense_umma(Geom g, Bufs b, int
       const int nr = (int)(r0 >= rows ? 0 : (r0 + kUHalf <= rows ? kUHalf : rows - r0));
       const bool ok_t = mb_wait(su32(&tfull[a]), (unsigned)((i >> 1) & 1));
       const bool ok_x = ok_t && mb_wait(su32(&xfull[s]), (unsigned)((j / nstages) & 1));
-      unsigned allok;  // AND over the warpgroup (named barrier 1 + h): it leaves together
-      asm volatile(
-          "{\n\t.reg .pred pi, po;\n\tsetp.ne.u32 pi, %1, 0;\n\tbar.red.and.pred po, %2, 128, pi;\n\t"
-          "selp.u32 %0, 1, 0, po;\n\t}"
-          : "=r"(allok)
-          : "r"((ok_t && ok_x) ? 1u : 0u), "r"(1 + h)
-          : "memory");
+      // AND over the warpgroup: its threads leave together
+      const bool allok = h == 0 ? wg_and<1>(ok_t && ok_x) : wg_and<2>(ok_t && ok_x);
       if (!allok) {
         if (et == 0) ep_abort = 1;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // this warp's 8 accumulator columns of every block, one wait
-      unsigned l[kUMaxCb][kUHalf];
+      // this warp's 8 accumulator columns of each block, kUGroup blocks per wait; the accumulator
+      // goes back to the MMA warp after the last group's loads
       const unsigned tq = tmem + ((unsigned)(q * 32) << 16) + (unsigned)(a * (kUTmemCols / 2) + h * kUHalf);
-#pragma unroll
-      for (int cb = 0; cb < kUMaxCb; ++cb)
-        if (cb < nq)
-          asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                       : "=r"(l[cb][0]), "=r"(l[cb][1]), "=r"(l[cb][2]), "=r"(l[cb][3]), "=r"(l[cb][4]),
-                         "=r"(l[cb][5]), "=r"(l[cb][6]), "=r"(l[cb][7])
-                       : "r"(tq + (unsigned)(cb * kURows)));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&tempty[a])) : "memory");
       float* stg = ring + (size_t)s * stage_f;
+      bool freed = false;
 #pragma unroll
-      for (int cb = 0; cb < kUMaxCb; ++cb) {
-        const int col = cb * kUCols + q * 32 + lane;
-        if (cb < nq && col < dn) {
-          float* p = stg + col;
-          if (nr == kUHalf) {
+      for (int g0 = 0; g0 < kUMaxCb; g0 += kUGroup) {
+        if (g0 >= nq) break;  // warp-uniform
+        unsigned l[kUGroup][kUHalf];
+        tmem_group(tq, g0, nq, l);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (g0 + kUGroup >= nq) {
+          release_acc(&tempty[a], lane);
+          freed = true;
+        }
 #pragma unroll
-            for (int r = 0; r < kUHalf; ++r) {
-              const float dl = p[r * dn] - __uint_as_float(l[cb][r]);
-              const float ad = fabsf(dl);
-              const bool keep = ad > zf;
-              p[r * dn] = keep ? dl : 0.f;
-              res = keep ? res : fmaf(dl, dl, res);
-              nnz += keep ? 1u : 0u;
-              inb += (fabsf(ad - zf) <= band) ? 1u : 0u;
-            }
-          } else {
+        for (int c = 0; c < kUGroup; ++c) {
+          const int col = (g0 + c) * kUCols + q * 32 + lane;
+          if (g0 + c < nq && col < dn) {
+            float* p = stg + col;
+            if (nr == kUHalf) {
 #pragma unroll
-            for (int r = 0; r < kUHalf; ++r) {
-              if (r < nr) {
-                const float dl = p[r * dn] - __uint_as_float(l[cb][r]);
-                const float ad = fabsf(dl);
-                const bool keep = ad > zf;
-                p[r * dn] = keep ? dl : 0.f;
-                res = keep ? res : fmaf(dl, dl, res);
-                nnz += keep ? 1u : 0u;
-                inb += (fabsf(ad - zf) <= band) ? 1u : 0u;
-              }
+              for (int r = 0; r < kUHalf; ++r) ht1(p + r * dn, l[c][r], zf, band, res, nnz, inb);
+            } else {
+#pragma unroll
+              for (int r = 0; r < kUHalf; ++r)
+                if (r < nr) ht1(p + r * dn, l[c][r], zf, band, res, nnz, inb);
             }
           }
         }
       }
+      if (!freed) release_acc(&tempty[a], lane);  // no column of this quarter
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // S half tile -> bulk store
-      asm volatile("bar.sync %0, 128;" ::"r"(1 + h) : "memory");
+      if (h == 0) wg_sync<1>();
+      else wg_sync<2>();
       if (et == 0) {
         if (nr > 0)
           asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(S + r0 * dn),
