@@ -18,7 +18,8 @@
 //   * two epilogue warpgroups, warpgroup h on rows 8h..8h+7 of every tile: tcgen05.ld of its 8
 //     accumulator columns per block (warp w reads TMEM lanes 32(w%4)..: 32 columns of X), X from
 //     its half stage, threshold, S written in place; the half tile leaves in one 1-D bulk store and
-//     its stage is refilled once that store has read it. The residual / nnz / band sums are fused.
+//     its stage is refilled once that store has read it (checked at the warpgroup's next store). The
+//     residual / nnz / band sums are fused.
 // Forms (FP32 accumulation in both):
 //   BF16: kind::f16 with BF16 operands split x = hi + lo, the three significant products
 //         B_hi T_hi + B_hi T_lo + B_lo T_hi packed along K = 16 (3 r_n <= 15); the dropped lo*lo
