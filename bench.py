@@ -381,11 +381,12 @@ def run_ours(a, rank, world):
         rt.rtcur_threshold_dense(plan, 1, sh)  # FP32 form at the plan's current state
         torch.cuda.synchronize()
         S_ref.copy_(S)
-        for name, form in (("fp32_plain", rt.FORM_FP32_PLAIN), ("bf16", rt.FORM_BF16),
-                           ("tf32", rt.FORM_TF32)):
+        for name, form, sfmt in (("fp32_plain", rt.FORM_FP32_PLAIN, rt.S_DENSE), ("bf16", rt.FORM_BF16, rt.S_DENSE),
+                                 ("tf32", rt.FORM_TF32, rt.S_DENSE),
+                                 ("fp32_compressed_S", rt.FORM_FP32, rt.S_COMPRESSED)):
             try:
                 fp = rt.rtcur_create(p.dims, p.ranks, p.m, p.q, p.zeta0, p.gamma, p.tol, max_iter,
-                                     variant, rt.make_options(scope=scope, dense_form=form))
+                                     variant, rt.make_options(scope=scope, dense_form=form, s_format=sfmt))
             except rt.RTCURError as exc:
                 forms_out[name] = {"unavailable": str(exc)}
                 continue
@@ -405,13 +406,25 @@ def run_ours(a, rank, world):
             ev1.record(stream)
             torch.cuda.synchronize()
             dms_f = ev0.elapsed_time(ev1) / 5
+            N = float(np.prod(p.dims))
+            fbytes, extra = 8.0 * N, {}
+            if sfmt == rt.S_COMPRESSED:
+                c = rt.rtcur_get_s_compressed(fp, sh)
+                # read X, write the nonzero values and the mask words
+                fbytes = 4.0 * N + 4.0 * c["nnz"] + 4.0 * c["rows"] * c["words_per_row"]
+                rt.rtcur_decode_s(fp, Sf.data_ptr(), sh)
+                torch.cuda.synchronize()
+                extra = {"nnz": c["nnz"], "bytes_per_element": fbytes / N,
+                         "S_bit_equal_to_fp32": bool(torch.equal(Sf, S_ref))}
             mism = int(((Sf != 0) != (S_ref != 0)).sum().item())
             rt.rtcur_destroy(fp)
             forms_out[name] = {"iters_per_s": K / (fms / 1e3), "ms_per_iter": fms / K,
                                "dense_ms": dms_f,
-                               "dense_gbs": 8.0 * float(np.prod(p.dims)) / (dms_f / 1e3) / 1e9,
+                               "dense_gbs": fbytes / (dms_f / 1e3) / 1e9,
                                "S_support_mismatch_vs_fp32": mism,
-                               "note": "same CUR iterates as the FP32 form; only S differs, near the threshold"}
+                               "note": "same CUR iterates as the FP32 form; only S differs, near the threshold"
+                                       if sfmt == rt.S_DENSE else
+                                       "the FP32 form with S written as support bitmask + nonzero values", **extra}
         forms_out["fp32_fused"] = {"iters_per_s": value / world, "ms_per_iter": ms / K,
                                    "dense_ms": roof["ms_per_launch"] if roof else None}
     # --- time to tolerance: whole solve from X resident, one graph launch; median of 5 after 2 ---

@@ -63,6 +63,12 @@ enum { RTCUR_SCOPE_SAMPLED = 0, RTCUR_SCOPE_FULL = 1 }; /* Eq. partial S update 
  * BF16 / TF32: the factored product on tcgen05 tensor cores with FP32 accumulation. */
 enum { RTCUR_FORM_FP32 = 0, RTCUR_FORM_FP32_PLAIN = 1, RTCUR_FORM_BF16 = 2, RTCUR_FORM_TF32 = 3 };
 
+/* Output format of S^(k) in the FULL scope (the tensor the dense pass writes every iteration).
+ * DENSE: prod d_i floats (default). COMPRESSED: the support as a bitmask plus the nonzero values
+ * (rtcur_s_compressed); the method is unchanged, only the bytes written drop (at 30% density from
+ * 4 to 1.33 bytes per element). Needs dense_form FP32, d_n % 4 == 0, d_n <= 4096, r_n <= 8. */
+enum { RTCUR_S_DENSE = 0, RTCUR_S_COMPRESSED = 1 };
+
 /* Bits of rtcur_result.flags */
 enum {
   RTCUR_FLAG_RANK_DEFICIENT = 1, /* some SVD_{r_i} kept fewer than r_i singular values */
@@ -84,8 +90,29 @@ typedef struct rtcur_options {
   int32_t refine_cluster;    /* CTAs per mode in the FP64 pinv refinement (a thread-block
                                 cluster): 0 = auto (16, else 8), or 2, 4, 8, 16; smaller clusters
                                 suit many concurrent problems (the batched form) */
-  int32_t reserved[5];       /* must be zero */
+  int32_t s_format;          /* RTCUR_S_*: format of S in the FULL scope; default DENSE */
+  int32_t reserved[4];       /* must be zero */
 } rtcur_options;
+
+/* Compressed S^(k) (s_format COMPRESSED), in device memory owned by the plan and overwritten by
+ * the next dense pass. The tensor is viewed as `rows` = prod_{i<n} d_i rows of `cols` = d_n
+ * elements (row-major, the last mode fastest: element e is row e / d_n, column e % d_n).
+ *   mask   rows * words_per_row words; bit b of mask[r * words_per_row + w] is set iff
+ *          S(r, 32 w + b) != 0 (bits at columns >= d_n are zero)
+ *   vals   for each block of block_cols = 128 columns of a row (the last one may be shorter):
+ *          its nonzero values, in column order, from the block's first element index on, i.e.
+ *          the j-th nonzero of block k of row r is vals[r * cols + 128 k + j]; the rest of the
+ *          block's range is not written
+ * rtcur_compact_s packs all nonzeros into one array in element order (CSR-like). */
+typedef struct rtcur_s_compressed {
+  const uint32_t* mask;
+  const float* vals;
+  int64_t nnz;           /* nonzeros of S^(k) */
+  int64_t rows;
+  int64_t cols;
+  int64_t words_per_row; /* ceil(d_n / 32) */
+  int64_t block_cols;    /* 128 */
+} rtcur_s_compressed;
 
 typedef struct rtcur_result {
   int32_t iters;        /* k at exit */
@@ -178,6 +205,30 @@ RTCUR_API rtcur_status rtcur_threshold_dense_noalloc(int32_t n_modes, const int6
                                                      const int32_t* ranks, const float* G,
                                                      const float* B, const float* X, double zeta,
                                                      float* S, double* counts, void* stream);
+
+/* rtcur_get_s_compressed -- describe the compressed S^(k) = HT_{zeta^(k)}(X - L^(k-1)) of the
+ * last dense pass (Sec. 3.2, Eq. S=HT(X-L); the FULL scope's S output) of a plan created with
+ * s_format COMPRESSED. Fills `out` with device pointers into the plan (valid until the next
+ * dense pass or rtcur_destroy) and the layout above. Synchronises `stream`.
+ * Errors: RTCUR_EINVAL (NULL plan or out, another s_format, no rtcur_begin, or k = 0: no dense
+ * pass has run and S^(0) = 0), RTCUR_ECUDA. */
+RTCUR_API rtcur_status rtcur_get_s_compressed(rtcur_plan* plan, rtcur_s_compressed* out, void* stream);
+
+/* rtcur_compact_s -- the nonzeros of the compressed S^(k) in element order (CSR-like with the
+ * mask: the j-th set bit of the mask, in row-major order, is vals_out[j]).
+ *   vals_out  device, >= nnz floats, or NULL
+ *   row_off   device, rows + 1 int64, or NULL: row r's first index in vals_out; the last entry
+ *             is nnz
+ * At least one of the two must be given. Synchronises `stream` once to read k; the copies run
+ * on `stream`. Errors: RTCUR_EINVAL (NULL plan or both outputs, another s_format, no
+ * rtcur_begin, k = 0), RTCUR_ECUDA. */
+RTCUR_API rtcur_status rtcur_compact_s(rtcur_plan* plan, float* vals_out, int64_t* row_off, void* stream);
+
+/* rtcur_decode_s -- expand the compressed S^(k) into a dense tensor.
+ *   S_out  device, prod d_i floats (any 4-byte alignment); receives zeros when k = 0
+ * rtcur_finish (and rtcur_solve) do the same when given S_out. Synchronises `stream` once to
+ * read k. Errors: RTCUR_EINVAL (NULL arguments, another s_format, no rtcur_begin), RTCUR_ECUDA. */
+RTCUR_API rtcur_status rtcur_decode_s(rtcur_plan* plan, float* S_out, void* stream);
 
 /* rtcur_get_factors -- copy the current L^(k) in Tucker form L = G x_1 B_1 ... x_n B_n to host
  * arrays (FP32): G has prod r_i entries (row-major), B_i is d_i x r_i row-major, packed mode

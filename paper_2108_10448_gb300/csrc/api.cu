@@ -263,7 +263,7 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
   o.inband_rel = 1e-6;
   if (opt) {
     o = *opt;
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < 4; ++i)
       if (o.reserved[i] != 0) return fail(nullptr, RTCUR_EINVAL, "options.reserved must be zero");
     if (o.refine_steps == 0 && o.jacobi_max_sweeps == 0 && o.inband_rel == 0.0) {
       o.refine_steps = 2; o.jacobi_max_sweeps = 30; o.inband_rel = 1e-6;
@@ -280,6 +280,10 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
     return fail(nullptr, RTCUR_EINVAL, "refine_cluster must be 0 (auto), 2, 4, 8 or 16");
   if (o.checkpoint < 0 || o.checkpoint > max_iter) return fail(nullptr, RTCUR_EINVAL, "checkpoint must be in [0, max_iter]");
   if (o.checkpoint > 0 && n_modes != 3) return fail(nullptr, RTCUR_EINVAL, "checkpoint (the adjoint) needs n_modes == 3");
+  if (o.s_format != RTCUR_S_DENSE && o.s_format != RTCUR_S_COMPRESSED)
+    return fail(nullptr, RTCUR_EINVAL, "s_format must be DENSE (0) or COMPRESSED (1)");
+  if (o.s_format == RTCUR_S_COMPRESSED && (o.scope != RTCUR_SCOPE_FULL || o.dense_form != RTCUR_FORM_FP32))
+    return fail(nullptr, RTCUR_EINVAL, "s_format COMPRESSED needs the FULL scope and dense_form FP32");
 
   Geom g;
   memset(&g, 0, sizeof g);
@@ -345,6 +349,7 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
   g.sumB = oB;
   g.sumMR = oQ;
   g.dense_form = o.dense_form;
+  g.s_format = o.s_format;
   {
     long long oDM = 0;
     for (int i = 0; i < n_modes; ++i) { g.offDM[i] = oDM; oDM += g.d[i] * g.m[i]; }
@@ -377,6 +382,8 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
 
   if (g.rowsT >= (1LL << 32) || g.d[n_modes - 1] >= (1LL << 32))
     return fail(nullptr, RTCUR_EINVAL, "prod of the first n-1 dims and the last dim must be < 2^32");
+  if (g.s_format == RTCUR_S_COMPRESSED && !compressed_geometry(g, g.tile_rows))
+    return fail(nullptr, RTCUR_EINVAL, "s_format COMPRESSED needs d_n %% 4 == 0, d_n <= 4096 and r_n <= 8");
   int dev = 0, optin = 0;
   cudaError_t ce = cudaGetDevice(&dev);
   if (ce != cudaSuccess) return fail(nullptr, RTCUR_ECUDA, "no CUDA device: %s", cudaGetErrorString(ce));
@@ -438,7 +445,14 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
   AL(b.tl, 4096);
   AL(b.tl_n, 1);
 #endif
-  if (o.scope == RTCUR_SCOPE_FULL) AL(p->S_internal, g.N);
+  if (o.scope == RTCUR_SCOPE_FULL && g.s_format == RTCUR_S_DENSE) AL(p->S_internal, g.N);
+  if (g.s_format == RTCUR_S_COMPRESSED) {
+    const long long wpr = (g.d[n_modes - 1] + 31) / 32;
+    AL(b.smask, g.rowsT * wpr);
+    AL(b.svals, g.N);
+    AL(b.srow, g.rowsT + 1);
+    AL(b.soff, (g.rowsT + 1) / 1023 + 64);
+  }
   if (o.scope == RTCUR_SCOPE_FULL && o.dense_form == RTCUR_FORM_FP32_PLAIN) {
     AL(b.Ap[0], g.sumDM);
     AL(b.Ap[1], g.sumDM);
@@ -525,7 +539,8 @@ rtcur_status rtcur_begin(rtcur_plan* p, const float* X, const int64_t* idx, floa
   if (!p) return fail(nullptr, RTCUR_EINVAL, "plan is NULL");
   if (!X || !idx) return fail(p, RTCUR_EINVAL, "X and idx must not be NULL");
   const Geom& g = p->g;
-  float* S = S_work ? S_work : p->S_internal;
+  const bool compressed = (g.s_format == RTCUR_S_COMPRESSED);
+  float* S = compressed ? nullptr : (S_work ? S_work : p->S_internal);
   if (!aligned16(X) || (S && !aligned16(S))) return fail(p, RTCUR_EINVAL, "X and S must be 16-byte aligned");
   rtcur_status st = check_sets(p, idx);
   if (st != RTCUR_OK) return st;
@@ -584,14 +599,18 @@ rtcur_status rtcur_finish(rtcur_plan* p, float* L_out, float* S_out, rtcur_resul
   const Bufs& b = p->b;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const bool full = (g.scope == RTCUR_SCOPE_FULL);
+  const bool compressed = (g.s_format == RTCUR_S_COMPRESSED);
   CKC(p, launch_materialize(g, b, L_out, full ? nullptr : S_out, s));
-  if (full && S_out && S_out != p->S_work)
+  if (full && !compressed && S_out && S_out != p->S_work)
     CKC(p, cudaMemcpyAsync(S_out, p->S_work, sizeof(float) * g.N, cudaMemcpyDeviceToDevice, s));
   State h;
   CKC(p, cudaMemcpyAsync(&h, b.st, sizeof h, cudaMemcpyDeviceToHost, s));
   CKC(p, cudaStreamSynchronize(s));
   if (full && S_out && h.k == 0) {  // no dense pass ran: S^(0) = 0
     CKC(p, cudaMemsetAsync(S_out, 0, sizeof(float) * g.N, s));
+    CKC(p, cudaStreamSynchronize(s));
+  } else if (full && S_out && compressed) {  // expand the last pass's compressed S
+    CKC(p, launch_decode_s(g, b, S_out, s));
     CKC(p, cudaStreamSynchronize(s));
   }
   int nh = h.k < g.max_iter ? h.k : g.max_iter;
@@ -676,6 +695,61 @@ rtcur_status rtcur_threshold_dense(rtcur_plan* p, int32_t n_launch, void* stream
   if (n_launch < 0) return fail(p, RTCUR_EINVAL, "n_launch must be >= 0");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   for (int i = 0; i < n_launch; ++i) CKC(p, launch_dense(p->g, p->b, p->opt.dense_form, s));
+  return RTCUR_OK;
+}
+
+rtcur_status rtcur_get_s_compressed(rtcur_plan* p, rtcur_s_compressed* out, void* stream) {
+  if (!p) return fail(nullptr, RTCUR_EINVAL, "plan is NULL");
+  if (!out) return fail(p, RTCUR_EINVAL, "out must not be NULL");
+  const Geom& g = p->g;
+  if (g.s_format != RTCUR_S_COMPRESSED) return fail(p, RTCUR_EINVAL, "the plan's s_format is not COMPRESSED");
+  if (!p->begun) return fail(p, RTCUR_EINVAL, "rtcur_begin must come first");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  State h;
+  CKC(p, cudaMemcpyAsync(&h, p->b.st, sizeof h, cudaMemcpyDeviceToHost, s));
+  CKC(p, cudaStreamSynchronize(s));
+  if (h.k == 0) return fail(p, RTCUR_EINVAL, "no dense pass has run (S^(0) = 0)");
+  memset(out, 0, sizeof *out);
+  out->mask = p->b.smask;
+  out->vals = p->b.svals;
+  out->nnz = h.nnz_f;
+  out->rows = g.rowsT;
+  out->cols = g.d[g.n - 1];
+  out->words_per_row = (g.d[g.n - 1] + 31) / 32;
+  out->block_cols = 128;
+  return RTCUR_OK;
+}
+
+rtcur_status rtcur_compact_s(rtcur_plan* p, float* vals_out, int64_t* row_off, void* stream) {
+  if (!p) return fail(nullptr, RTCUR_EINVAL, "plan is NULL");
+  if (!vals_out && !row_off) return fail(p, RTCUR_EINVAL, "vals_out and row_off are both NULL");
+  const Geom& g = p->g;
+  if (g.s_format != RTCUR_S_COMPRESSED) return fail(p, RTCUR_EINVAL, "the plan's s_format is not COMPRESSED");
+  if (!p->begun) return fail(p, RTCUR_EINVAL, "rtcur_begin must come first");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  State h;
+  CKC(p, cudaMemcpyAsync(&h, p->b.st, sizeof h, cudaMemcpyDeviceToHost, s));
+  CKC(p, cudaStreamSynchronize(s));
+  if (h.k == 0) return fail(p, RTCUR_EINVAL, "no dense pass has run (S^(0) = 0)");
+  long long* off = row_off ? reinterpret_cast<long long*>(row_off) : p->b.srow;
+  CKC(p, launch_compact_s(g, p->b, off, vals_out, s));
+  return RTCUR_OK;
+}
+
+rtcur_status rtcur_decode_s(rtcur_plan* p, float* S_out, void* stream) {
+  if (!p) return fail(nullptr, RTCUR_EINVAL, "plan is NULL");
+  if (!S_out) return fail(p, RTCUR_EINVAL, "S_out must not be NULL");
+  const Geom& g = p->g;
+  if (g.s_format != RTCUR_S_COMPRESSED) return fail(p, RTCUR_EINVAL, "the plan's s_format is not COMPRESSED");
+  if (!p->begun) return fail(p, RTCUR_EINVAL, "rtcur_begin must come first");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  State h;
+  CKC(p, cudaMemcpyAsync(&h, p->b.st, sizeof h, cudaMemcpyDeviceToHost, s));
+  CKC(p, cudaStreamSynchronize(s));
+  if (h.k == 0)
+    CKC(p, cudaMemsetAsync(S_out, 0, sizeof(float) * g.N, s));
+  else
+    CKC(p, launch_decode_s(g, p->b, S_out, s));
   return RTCUR_OK;
 }
 

@@ -9,6 +9,7 @@
 // for the whole launch, so the inner loop reads only X, one broadcast row of T, and writes S.
 // Blocks use few threads per SM so that the latency-bound sampled chain, which runs
 // concurrently on its own graph branch, finds room.
+#include "../../include/rtcur.h"
 #include "rtcur_internal.cuh"
 
 namespace {
@@ -156,6 +157,7 @@ __global__ void __launch_bounds__(512) k_dense_fp32(Geom g, Bufs b) {
 // copies (again bounded) and returns.
 constexpr int kStages = 4;
 constexpr long long kSpinLimit = 1LL << 26;
+constexpr int kRowGroupsCompressed = 2;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
@@ -204,10 +206,37 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
       : "memory");
 }
 
+// Compressed output of one row of S held by a warp: thread c4 (lane of warp w) owns columns
+// 4 c4 .. 4 c4 + 3, so the warp owns the row's 128-column block w. Each lane's 4-bit keep nibble,
+// shifted to its place and OR-reduced over groups of 8 lanes, gives the block's four mask words
+// (word k from lanes 8k .. 8k + 7); four ballots give each kept value's rank in the block, and the
+// values go, in order, from the block's first element on (vblk). Called by all 32 lanes of the
+// warp (inactive lanes pass 0).
+__device__ __forceinline__ void emit_row(unsigned* mrow, float* vblk, float4 sv, int wpr, int wid, int lane) {
+  const bool k0 = sv.x != 0.f, k1 = sv.y != 0.f, k2 = sv.z != 0.f, k3 = sv.w != 0.f;
+  unsigned w = ((unsigned)k0 | ((unsigned)k1 << 1) | ((unsigned)k2 << 2) | ((unsigned)k3 << 3)) << (4 * (lane & 7));
+  w |= __shfl_xor_sync(0xffffffffu, w, 1);
+  w |= __shfl_xor_sync(0xffffffffu, w, 2);
+  w |= __shfl_xor_sync(0xffffffffu, w, 4);
+  const int wk = 4 * wid + (lane >> 3);
+  if ((lane & 7) == 0 && wk < wpr) mrow[wk] = w;
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned rk = __popc(__ballot_sync(0xffffffffu, k0) & lt) + __popc(__ballot_sync(0xffffffffu, k1) & lt) +
+                __popc(__ballot_sync(0xffffffffu, k2) & lt) + __popc(__ballot_sync(0xffffffffu, k3) & lt);
+  if (k0) vblk[rk++] = sv.x;
+  if (k1) vblk[rk++] = sv.y;
+  if (k2) vblk[rk++] = sv.z;
+  if (k3) vblk[rk] = sv.w;
+}
+
 // MODE 0: the fused threshold pass of an iteration (L^(k), zeta^(k+1), S into the solve's S
 //         buffer, reductions). MODE 1: write L of copy `copy_sel` (0 = current, 1 = previous)
 //         into `out` (no X read). MODE 2: write HT_{zeta^(k)}(X - L) of copy `copy_sel` into
 //         `out` (zero when k = 0). Modes 1 and 2 materialise the solve's outputs.
+// MODE 3: MODE 0 with S written compressed instead of dense: the support as bitmask words (bit
+//         b of word w of row r is S(r, 32 w + b) != 0) and, for each 128-column block of a row,
+//         its nonzero values in order from the block's first element index on. At 30% density
+//         that is 4 + 1/8 + 1.2 bytes per element instead of 8.
 template <int RN, int MODE>
 __global__ void __launch_bounds__(1024, 1) k_dense_tma(Geom g, Bufs b, int tr, int copy_sel, float* out) {
   TL_BEGIN();
@@ -217,13 +246,14 @@ __global__ void __launch_bounds__(1024, 1) k_dense_tma(Geom g, Bufs b, int tr, i
   __shared__ int abort_flag;
   const State* st = b.st;
   const int kk = st->k;
-  const int cur = (MODE == 0) ? (kk & 1) : ((kk + copy_sel) & 1);
-  const double zeta = (MODE == 0) ? g.gamma * st->zeta : st->zeta;
+  constexpr bool kFused = (MODE == 0 || MODE == 3);  // the iteration's threshold pass
+  const int cur = kFused ? (kk & 1) : ((kk + copy_sel) & 1);
+  const double zeta = kFused ? g.gamma * st->zeta : st->zeta;
   const float zf = (float)zeta;
   const float band = (float)(g.inband * zeta);
   const bool zero_out = (MODE == 2) && (kk == 0);
   const float* __restrict__ X = b.sp->X;
-  float* __restrict__ S = (MODE == 0) ? b.sp->S : out;
+  float* __restrict__ S = (MODE == 0) ? b.sp->S : out;  // unused by MODE 3
   const float* __restrict__ T = b.T[cur];
   const float* __restrict__ Bn = b.B[cur] + g.offB[g.n - 1];
   const long long dn = g.d[g.n - 1];
@@ -236,7 +266,13 @@ __global__ void __launch_bounds__(1024, 1) k_dense_tma(Geom g, Bufs b, int tr, i
   // T rows of a tile: floats [r0*RN rounded down to 4, (r0+nr)*RN rounded up to 4)
   const int tstage = ((tr * RN + 3) & ~3) + 4;
   float* tring = reinterpret_cast<float*>(ring + (size_t)kStages * stage_f4);
-  const int c4 = threadIdx.x;
+  // blockDim.x = G row groups of rowT threads: thread c4 of group grp owns float4 column c4 of
+  // rows grp, grp + G, ... of each tile (G > 1 gives the latency-bound row loop more warps)
+  const int rowT = ((n4 + 31) / 32) * 32;
+  const int G = (int)blockDim.x / rowT;
+  const int grp = (int)threadIdx.x / rowT;
+  const int c4 = (int)threadIdx.x - grp * rowT;
+  const int wpr = (int)((dn + 31) >> 5);  // MODE 3: mask words per row
   float br[4][RN];
   if (c4 < n4) {
 #pragma unroll
@@ -289,38 +325,60 @@ __global__ void __launch_bounds__(1024, 1) k_dense_tma(Geom g, Bufs b, int tr, i
     if (abort_flag) break;
     const long long r0 = t * tr;
     const int nr = (int)(r0 + tr <= rows ? tr : rows - r0);
-    if (c4 < n4) {
+    if (MODE == 3 || c4 < n4) {  // MODE 3: whole warps, for the ballots of the compressed rows
+      const bool act = c4 < n4;
       const float4* tile = ring + (size_t)s * stage_f4;
       const float* ttile = tring + (size_t)s * tstage + (r0 * RN - ((r0 * RN) & ~3LL));
-      for (int rr = 0; rr < nr; ++rr) {
-        float tv[RN];
+      for (int rr = grp; rr < nr; rr += G) {
+        float4 sv = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (act) {
+          float tv[RN];
 #pragma unroll
-        for (int c = 0; c < RN; ++c) tv[c] = ttile[rr * RN + c];
-        float L0 = 0.f, L1 = 0.f, L2 = 0.f, L3 = 0.f;
+          for (int c = 0; c < RN; ++c) tv[c] = ttile[rr * RN + c];
+          float L0 = 0.f, L1 = 0.f, L2 = 0.f, L3 = 0.f;
 #pragma unroll
-        for (int c = 0; c < RN; ++c) {
-          L0 = fmaf(tv[c], br[0][c], L0);
-          L1 = fmaf(tv[c], br[1][c], L1);
-          L2 = fmaf(tv[c], br[2][c], L2);
-          L3 = fmaf(tv[c], br[3][c], L3);
+          for (int c = 0; c < RN; ++c) {
+            L0 = fmaf(tv[c], br[0][c], L0);
+            L1 = fmaf(tv[c], br[1][c], L1);
+            L2 = fmaf(tv[c], br[2][c], L2);
+            L3 = fmaf(tv[c], br[3][c], L3);
+          }
+          if (MODE == 1) {
+            sv = make_float4(L0, L1, L2, L3);
+          } else {
+            float4 xv = tile[rr * n4 + c4];
+            ht_acc(xv.x, L0, zf, band, sv.x, res, nnz, inb);
+            ht_acc(xv.y, L1, zf, band, sv.y, res, nnz, inb);
+            ht_acc(xv.z, L2, zf, band, sv.z, res, nnz, inb);
+            ht_acc(xv.w, L3, zf, band, sv.w, res, nnz, inb);
+            if (zero_out) sv = make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+          if (MODE != 3) const_cast<float4*>(tile)[rr * n4 + c4] = sv;  // in place: one copy out
         }
-        float4 sv;
-        if (MODE == 1) {
-          sv = make_float4(L0, L1, L2, L3);
-        } else {
-          float4 xv = tile[rr * n4 + c4];
-          ht_acc(xv.x, L0, zf, band, sv.x, res, nnz, inb);
-          ht_acc(xv.y, L1, zf, band, sv.y, res, nnz, inb);
-          ht_acc(xv.z, L2, zf, band, sv.z, res, nnz, inb);
-          ht_acc(xv.w, L3, zf, band, sv.w, res, nnz, inb);
-          if (zero_out) sv = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        const_cast<float4*>(tile)[rr * n4 + c4] = sv;  // in place: the tile goes out in one copy
+        if (MODE == 3)
+          emit_row(b.smask + (r0 + rr) * wpr, b.svals + (r0 + rr) * dn + (c4 & ~31) * 4, sv, wpr, c4 >> 5,
+                   (int)(threadIdx.x & 31));
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // stage writes -> bulk store
     __syncthreads();  // stage s fully consumed and holding the output rows
-    if (threadIdx.x == 0) {
+    if (MODE == 3) {  // the stage is read: refill it with the tile kStages ahead
+      if (threadIdx.x == 0) {
+        const long long tn = t + (long long)kStages * gridDim.x;
+        if (tn < ntiles) {
+          long long rn0 = tn * tr;
+          long long nr2 = (rn0 + tr <= rows ? tr : rows - rn0);
+          unsigned bytes = (unsigned)(nr2 * dn * 4);
+          long long a0 = (rn0 * RN) & ~3LL, a1 = ((rn0 + nr2) * RN + 3) & ~3LL;
+          unsigned tbytes = (unsigned)((a1 - a0) * 4);
+          mbar_expect_tx(&full[s], bytes + tbytes);
+          bulk_g2s_stream(ring + (size_t)s * stage_f4, X + rn0 * dn, bytes, &full[s]);
+          bulk_g2s(tring + (size_t)s * tstage, T + a0, tbytes, &full[s]);
+#pragma unroll
+          for (int s2 = 0; s2 < kStages; ++s2) issued[s2] += (s2 == s) ? 1 : 0;
+        }
+      }
+    } else if (threadIdx.x == 0) {
       // the tile's output rows leave in one bulk copy; the stage of the previous tile, whose
       // store has now read it, is refilled with the tile kStages ahead of that one
       asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(S + r0 * dn),
@@ -360,7 +418,7 @@ __global__ void __launch_bounds__(1024, 1) k_dense_tma(Geom g, Bufs b, int tr, i
     __syncthreads();
   }
   (void)tile_bytes_full;
-  if (MODE != 0) return;
+  if (!kFused) return;
   double* part = b.red + (size_t)TK_DENSE * kMaxRedBlocks * RT_RED_SLOTS;
   const int bid = blockIdx.x;
   double t0 = block_sum_d((double)res, sh);
@@ -381,9 +439,11 @@ __global__ void __launch_bounds__(1024, 1) k_dense_tma(Geom g, Bufs b, int tr, i
         if (slot == 2) w->inband_f = (long long)acc;
       }
     }
-    if (threadIdx.x == 0) b.ticket[TK_DENSE] = 0u;
+    if (threadIdx.x == 0) {
+      b.ticket[TK_DENSE] = 0u;
+    }
   }
-  TL_END(1 + 20 * MODE);
+  TL_END(MODE == 3 ? 1 : 1 + 20 * MODE);
 }
 
 template <int RN>
@@ -391,6 +451,8 @@ cudaError_t launch_tma_rn(const Geom& g, const Bufs& b, int tr, size_t smem, int
                           cudaStream_t s, int mode = 0, int copy_sel = 0, float* out = nullptr) {
   if (mode == 0)
     k_dense_tma<RN, 0><<<grid, threads, smem, s>>>(g, b, tr, copy_sel, out);
+  else if (mode == 3)
+    k_dense_tma<RN, 3><<<grid, threads, smem, s>>>(g, b, tr, copy_sel, out);
   else if (mode == 1)
     k_dense_tma<RN, 1><<<grid, threads, smem, s>>>(g, b, tr, copy_sel, out);
   else
@@ -404,7 +466,8 @@ cudaError_t launch_tma_rn(const Geom& g, const Bufs& b, int tr, size_t smem, int
 template <int RN>
 cudaError_t prepare_tma_rn(size_t smem) {
   cudaError_t e = cudaSuccess;
-  void* fns[3] = {(void*)k_dense_tma<RN, 0>, (void*)k_dense_tma<RN, 1>, (void*)k_dense_tma<RN, 2>};
+  void* fns[4] = {(void*)k_dense_tma<RN, 0>, (void*)k_dense_tma<RN, 1>, (void*)k_dense_tma<RN, 2>,
+                  (void*)k_dense_tma<RN, 3>};
   for (void* f : fns) {
     if (e == cudaSuccess) e = raise_smem_limit((const void*)f, (size_t)(smem));
     if (e == cudaSuccess)
@@ -481,7 +544,129 @@ __global__ void __launch_bounds__(256) k_materialize(Geom g, Bufs b, float* L_ou
   }
 }
 
+// Expansion of the compressed S (MODE 3) into a dense tensor: one warp per row, one mask word
+// (32 columns) per step; a value's rank in its 128-column block is the bits before it in the
+// block's words.
+__global__ void __launch_bounds__(256) k_decode_s(Geom g, Bufs b, float* S_out) {
+  const long long row = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = (int)(threadIdx.x & 31);
+  if (row >= g.rowsT) return;
+  const long long dn = g.d[g.n - 1];
+  const int wpr = (int)((dn + 31) >> 5);
+  const unsigned* mrow = b.smask + row * wpr;
+  const float* vrow = b.svals + row * dn;
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned before = 0u;  // bits in the earlier words of the current block
+  for (int w = 0; w < wpr; ++w) {
+    if ((w & 3) == 0) before = 0u;
+    const unsigned m = mrow[w];
+    const long long c = 32LL * w + lane;
+    if (c < dn) S_out[row * dn + c] = ((m >> lane) & 1u) ? vrow[128 * (w >> 2) + before + __popc(m & lt)] : 0.f;
+    before += (unsigned)__popc(m);
+  }
+}
+
+// Nonzeros per row: cnt[row] = popcount of the row's mask words (one warp per row).
+__global__ void __launch_bounds__(256) k_row_counts(Geom g, Bufs b, long long* cnt) {
+  const long long row = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = (int)(threadIdx.x & 31);
+  if (row >= g.rowsT) return;
+  const int wpr = (int)((g.d[g.n - 1] + 31) >> 5);
+  unsigned c = 0u;
+  for (int w = lane; w < wpr; w += 32) c += (unsigned)__popc(b.smask[row * wpr + w]);
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (lane == 0) cnt[row] = c;
+}
+
+// Exclusive scan, in place, of v[0 .. n) in chunks of 1024 (one block per chunk); the chunk's
+// total goes to tot[chunk]. With add = 1 instead, each element gets tot[chunk] added.
+__global__ void __launch_bounds__(1024) k_scan_chunks(long long* v, long long n, long long* tot, int add) {
+  __shared__ long long wsum[32];
+  const long long i = (long long)blockIdx.x * 1024 + threadIdx.x;
+  if (add) {
+    if (i < n) v[i] += tot[blockIdx.x];
+    return;
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const long long c = i < n ? v[i] : 0;
+  long long x = c;
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    long long w = wsum[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    wsum[lane] = w;  // inclusive over the warps
+  }
+  __syncthreads();
+  const long long before = wid > 0 ? wsum[wid - 1] : 0;
+  if (i < n) v[i] = before + x - c;
+  if (threadIdx.x == 1023) tot[blockIdx.x] = before + x;
+}
+
+// Every row's values, block after block, to out[off[row] ...]: the nonzeros in element order
+// (one warp per row).
+__global__ void __launch_bounds__(256) k_compact_s(Geom g, Bufs b, const long long* off, float* out) {
+  const long long row = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = (int)(threadIdx.x & 31);
+  if (row >= g.rowsT) return;
+  const long long dn = g.d[g.n - 1];
+  const int wpr = (int)((dn + 31) >> 5);
+  const unsigned* mrow = b.smask + row * wpr;
+  const float* vrow = b.svals + row * dn;
+  long long o = off[row];
+  for (int blk = 0; 4 * blk < wpr; ++blk) {
+    unsigned n = 0u;
+    for (int w = 4 * blk; w < 4 * blk + 4 && w < wpr; ++w) n += (unsigned)__popc(mrow[w]);
+    for (unsigned i = lane; i < n; i += 32) out[o + i] = vrow[128 * blk + i];
+    o += n;
+  }
+}
+
 }  // namespace
+
+bool compressed_geometry(const Geom& g, int& tile_rows) {
+  int threads;
+  size_t smem;
+  int tr = 0;
+  if (!tma_geometry(g, tr, smem, threads)) return false;
+  tile_rows = tr;
+  return true;
+}
+
+cudaError_t launch_decode_s(const Geom& g, const Bufs& b, float* S_out, cudaStream_t s) {
+  k_decode_s<<<(unsigned)((g.rowsT + 7) / 8), 256, 0, s>>>(g, b, S_out);
+  return cudaGetLastError();
+}
+
+// Exclusive scan of v[0 .. n) in place; scratch holds n / 1023 + 64 entries (the chunk totals of
+// every level).
+cudaError_t scan_exclusive(long long* v, long long n, long long* scratch, cudaStream_t s) {
+  const long long nch = (n + 1023) / 1024;
+  k_scan_chunks<<<(unsigned)nch, 1024, 0, s>>>(v, n, scratch, 0);
+  if (nch == 1) return cudaGetLastError();
+  cudaError_t e = scan_exclusive(scratch, nch, scratch + nch, s);
+  if (e != cudaSuccess) return e;
+  k_scan_chunks<<<(unsigned)nch, 1024, 0, s>>>(v, n, scratch, 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_compact_s(const Geom& g, const Bufs& b, long long* off, float* out, cudaStream_t s) {
+  const long long rows = g.rowsT;
+  const unsigned blocks = (unsigned)((rows + 7) / 8);
+  cudaError_t e = cudaMemsetAsync(off + rows, 0, sizeof(long long), s);
+  if (e != cudaSuccess) return e;
+  k_row_counts<<<blocks, 256, 0, s>>>(g, b, off);
+  if ((e = scan_exclusive(off, rows + 1, b.soff, s)) != cudaSuccess || !out) return e;
+  k_compact_s<<<blocks, 256, 0, s>>>(g, b, off, out);
+  return cudaGetLastError();
+}
 
 bool dense_form_supported(const Geom& g, int form) {
   if (form == 0) return true;
@@ -516,6 +701,7 @@ cudaError_t launch_dense(const Geom& g, const Bufs& b, int form, cudaStream_t s)
   if (form == 2) return launch_umma(g, b, 0, s);
   if (form == 3) return launch_umma(g, b, 1, s);
   if (form != 0) return cudaErrorNotSupported;
+  if (g.s_format == RTCUR_S_COMPRESSED && g.tile_rows < 1) return cudaErrorNotSupported;
   {
     int tr, threads;
     size_t smem;
@@ -523,15 +709,19 @@ cudaError_t launch_dense(const Geom& g, const Bufs& b, int form, cudaStream_t s)
       long long ntiles = (g.rowsT + tr - 1) / tr;
       int ctas = g.dense_ctas > 0 ? g.dense_ctas : 144;
       int grid = (int)(ntiles < ctas ? ntiles : ctas);
+      const int mode = (g.s_format == RTCUR_S_COMPRESSED) ? 3 : 0;
+      // the compressed pass runs two row groups: twice the warps for its longer row loop, and
+      // still room beside it for a CTA of the sampled chain's refinement cluster
+      if (mode == 3 && 2 * threads <= 1024) threads *= kRowGroupsCompressed;
       switch (g.rlast) {
-        case 1: return launch_tma_rn<1>(g, b, tr, smem, grid, threads, s);
-        case 2: return launch_tma_rn<2>(g, b, tr, smem, grid, threads, s);
-        case 3: return launch_tma_rn<3>(g, b, tr, smem, grid, threads, s);
-        case 4: return launch_tma_rn<4>(g, b, tr, smem, grid, threads, s);
-        case 5: return launch_tma_rn<5>(g, b, tr, smem, grid, threads, s);
-        case 6: return launch_tma_rn<6>(g, b, tr, smem, grid, threads, s);
-        case 7: return launch_tma_rn<7>(g, b, tr, smem, grid, threads, s);
-        default: return launch_tma_rn<8>(g, b, tr, smem, grid, threads, s);
+        case 1: return launch_tma_rn<1>(g, b, tr, smem, grid, threads, s, mode);
+        case 2: return launch_tma_rn<2>(g, b, tr, smem, grid, threads, s, mode);
+        case 3: return launch_tma_rn<3>(g, b, tr, smem, grid, threads, s, mode);
+        case 4: return launch_tma_rn<4>(g, b, tr, smem, grid, threads, s, mode);
+        case 5: return launch_tma_rn<5>(g, b, tr, smem, grid, threads, s, mode);
+        case 6: return launch_tma_rn<6>(g, b, tr, smem, grid, threads, s, mode);
+        case 7: return launch_tma_rn<7>(g, b, tr, smem, grid, threads, s, mode);
+        default: return launch_tma_rn<8>(g, b, tr, smem, grid, threads, s, mode);
       }
     }
   }

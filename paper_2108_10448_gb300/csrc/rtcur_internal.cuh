@@ -42,6 +42,8 @@ struct Geom {
   int dense_ctas;                // persistent CTAs of the dense pass (0: default)
   int dense_form;                // RTCUR_FORM_* of the dense pass
   int ck_iters;                  // iterations recorded for the adjoint (0: none)
+  int s_format;                  // RTCUR_S_* of the FULL scope's S output
+  int tile_rows;                 // rows per tile of the FP32 bulk-copy pass (compressed S layout)
   int nG;                       // prod r_i
   int rlast;                    // r_n
   long long d[RT_MAXN];
@@ -145,6 +147,13 @@ struct Bufs {
   unsigned* tl_n;
   float* ckV;            // ck_iters * nS: sampled values X - S of each recorded iteration
   unsigned char* ckM;    // ck_iters * nS: their HT masks (1 = thresholded, the value is L^(k))
+  // compressed S (FULL scope, s_format COMPRESSED): support bitmask of rowsT rows of
+  // ceil(d_n / 32) words; the nonzero values of each 128-column block of a row, in order, from
+  // the block's first element index on; row offsets and scan scratch for the compaction
+  unsigned* smask;
+  float* svals;
+  long long* srow;   // rowsT + 1
+  long long* soff;   // (rowsT + 1) / 1023 + 64
 };
 
 // Workspace of the adjoint (rtcur_backward), 3-mode tensors. Per recorded iteration and mode:
@@ -167,6 +176,14 @@ struct BwWork {
   double* part;  // partsz: split-K partial sums
   long long tmpsz, partsz;
 };
+
+// compressed S: tile geometry of the FP32 bulk-copy pass (false: the format does not apply), and
+// the expansion of the last pass's compressed S into a dense tensor
+bool compressed_geometry(const Geom& g, int& tile_rows);
+cudaError_t launch_decode_s(const Geom& g, const Bufs& b, float* S_out, cudaStream_t s);
+// off (rowsT + 1) = exclusive prefix of the rows' nonzero counts; then, when out is given, every
+// nonzero in element order into out
+cudaError_t launch_compact_s(const Geom& g, const Bufs& b, long long* off, float* out, cudaStream_t s);
 
 // tensor-core (tcgen05) forms of the dense pass: kind 0 = BF16 split, 1 = TF32
 size_t umma_smem(const Geom& g, int kind);  // 0 when the form does not apply

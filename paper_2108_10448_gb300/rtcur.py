@@ -17,12 +17,19 @@ VARIANT_F, VARIANT_R = 0, 1
 SCOPE_SAMPLED, SCOPE_FULL = 0, 1
 FORM_FP32, FORM_FP32_PLAIN, FORM_BF16, FORM_TF32 = 0, 1, 2, 3
 FLAG_RANK_DEFICIENT, FLAG_TIE = 1, 2
+S_DENSE, S_COMPRESSED = 0, 1
 
 
 class rtcur_options(C.Structure):
     _fields_ = [("scope", C.c_int32), ("dense_form", C.c_int32), ("refine_steps", C.c_int32),
                 ("jacobi_max_sweeps", C.c_int32), ("inband_rel", C.c_double),
-                ("eig_method", C.c_int32), ("checkpoint", C.c_int32), ("refine_cluster", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("eig_method", C.c_int32), ("checkpoint", C.c_int32), ("refine_cluster", C.c_int32), ("s_format", C.c_int32),
+                ("reserved", C.c_int32 * 4)]
+
+
+class rtcur_s_compressed(C.Structure):
+    _fields_ = [("mask", C.c_void_p), ("vals", C.c_void_p), ("nnz", C.c_int64), ("rows", C.c_int64),
+                ("cols", C.c_int64), ("words_per_row", C.c_int64), ("block_cols", C.c_int64)]
 
 
 class rtcur_result(C.Structure):
@@ -69,6 +76,9 @@ def load(path=LIB_PATH):
     lib.rtcur_threshold_dense_noalloc.restype = C.c_int
     lib.rtcur_get_factors.argtypes = [P, C.POINTER(C.c_float), C.POINTER(C.c_float),
                                       C.POINTER(C.c_int32), C.POINTER(C.c_double), P]
+    lib.rtcur_get_s_compressed.argtypes = [P, C.POINTER(rtcur_s_compressed), P]
+    lib.rtcur_decode_s.argtypes = [P, P, P]
+    lib.rtcur_compact_s.argtypes = [P, P, P, P]
     lib.rtcur_sample_count.argtypes = [P]
     lib.rtcur_sample_count.restype = C.c_int64
     lib.rtcur_last_error.argtypes = [P]
@@ -76,7 +86,8 @@ def load(path=LIB_PATH):
     lib.rtcur_destroy.argtypes = [P]
     lib.rtcur_destroy.restype = None
     for f in ("rtcur_create", "rtcur_solve", "rtcur_begin", "rtcur_iterate", "rtcur_finish",
-              "rtcur_get_factors", "rtcur_threshold_dense", "rtcur_backward", "rtcur_solve_batched"):
+              "rtcur_get_factors", "rtcur_threshold_dense", "rtcur_backward", "rtcur_solve_batched",
+              "rtcur_get_s_compressed", "rtcur_decode_s", "rtcur_compact_s"):
         getattr(lib, f).restype = C.c_int
     _lib = lib
     return lib
@@ -104,12 +115,14 @@ EIG_TRIDIAGONAL, EIG_JACOBI = 0, 1
 
 
 def make_options(scope=SCOPE_SAMPLED, dense_form=FORM_FP32, refine_steps=2, jacobi_max_sweeps=30,
-                 inband_rel=1e-6, eig_method=EIG_TRIDIAGONAL, checkpoint=0, refine_cluster=0):
+                 inband_rel=1e-6, eig_method=EIG_TRIDIAGONAL, checkpoint=0, refine_cluster=0,
+                 s_format=S_DENSE):
     o = rtcur_options()
     o.scope, o.dense_form, o.refine_steps = scope, dense_form, refine_steps
     o.jacobi_max_sweeps, o.inband_rel, o.eig_method = jacobi_max_sweeps, inband_rel, eig_method
     o.checkpoint = checkpoint
     o.refine_cluster = refine_cluster
+    o.s_format = s_format
     return o
 
 
@@ -190,6 +203,25 @@ def rtcur_finish(plan, L_ptr=0, S_ptr=0, stream=0, max_iter=1000):
 
 def rtcur_threshold_dense(plan, n_launch=1, stream=0):
     _check(load().rtcur_threshold_dense(plan, int(n_launch), stream or None), plan)
+
+
+def rtcur_get_s_compressed(plan, stream=0):
+    """The compressed S^(k) of a plan with s_format S_COMPRESSED: a dict of device addresses
+    (mask, vals) and the layout fields of include/rtcur.h."""
+    out = rtcur_s_compressed()
+    _check(load().rtcur_get_s_compressed(plan, C.byref(out), stream or None), plan)
+    return {f: getattr(out, f) for f, _ in rtcur_s_compressed._fields_}
+
+
+def rtcur_compact_s(plan, vals_out=0, row_off=0, stream=0):
+    """All nonzeros of the compressed S^(k) in element order into the device buffer vals_out
+    (>= nnz floats) and/or the rows' exclusive prefix into row_off (rows + 1 int64)."""
+    _check(load().rtcur_compact_s(plan, vals_out or None, row_off or None, stream or None), plan)
+
+
+def rtcur_decode_s(plan, S_out, stream=0):
+    """Expand the compressed S^(k) into the dense device buffer at address S_out."""
+    _check(load().rtcur_decode_s(plan, S_out, stream or None), plan)
 
 
 def rtcur_solve_batched(plans, X_ptrs, idxs, L_ptrs=None, S_ptrs=None, stream=0, max_iter=1000):

@@ -74,3 +74,16 @@ def test_checkpoint_options_are_validated(lib):
                             rt.make_options(checkpoint=ck))
         assert ei.value.status == rt.EINVAL
         assert msg in str(ei.value)
+
+
+def test_s_format_options_are_validated(lib):
+    from paper_2108_10448_gb300 import rtcur as rt
+    for dims, kw, msg in (([8, 8, 8], dict(s_format=2), "s_format must be"),
+                          ([8, 8, 8], dict(s_format=rt.S_COMPRESSED), "needs the FULL scope"),
+                          ([8, 8, 8], dict(s_format=rt.S_COMPRESSED, scope=rt.SCOPE_FULL,
+                                           dense_form=rt.FORM_BF16), "dense_form FP32"),
+                          ([8, 8, 10], dict(s_format=rt.S_COMPRESSED, scope=rt.SCOPE_FULL), "d_n % 4 == 0")):
+        with pytest.raises(rt.RTCURError) as ei:
+            rt.rtcur_create(dims, [2, 2, 2], [4, 4, 4], [8, 8, 8], 1.0, 0.7, 1e-5, 5, 0, rt.make_options(**kw))
+        assert ei.value.status == rt.EINVAL
+        assert msg in str(ei.value)
