@@ -244,6 +244,7 @@ __global__ void __launch_bounds__(1024, 1) k_dense_tma(Geom g, Bufs b, int tr, i
   __shared__ unsigned long long full[kStages];
   __shared__ double sh[32];
   __shared__ int abort_flag;
+  __shared__ long long tile_of[kStages];     // tile held by each stage, -1: no more tiles
   const State* st = b.st;
   const int kk = st->k;
   constexpr bool kFused = (MODE == 0 || MODE == 3);  // the iteration's threshold pass
@@ -286,17 +287,43 @@ __global__ void __launch_bounds__(1024, 1) k_dense_tma(Geom g, Bufs b, int tr, i
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  // prologue: first kStages tiles of this CTA. Thread 0 alone issues copies and counts, per
-  // stage, the copies issued and the completions it has observed (for the bounded drain).
-  long long my_first = blockIdx.x;
+  // Tiles: the first kStages x grid go out statically (stage s of CTA c holds tile c + s grid).
+  // The compressed pass (MODE 3, ~3.7 us a tile) then hands out the rest from a counter, so CTAs
+  // that share their SM with the sampled chain's blocks take fewer tiles (1.73 -> 1.67 ms at
+  // 800^3). The other modes keep the static stride: at ~1.5 us a tile the counter's atomics,
+  // all on one L2 slice that every bulk copy also crosses, slowed the dense pass from 0.683 to
+  // 0.85 ms.
+  // Thread 0 alone issues copies and counts, per stage, the copies issued and the completions it
+  // has observed (for the bounded drain). In MODE 3 a stage past the last tile gets tile -1 and a
+  // plain arrive instead of a copy.
   int issued[kStages], seen[kStages];
 #pragma unroll
   for (int s = 0; s < kStages; ++s) issued[s] = seen[s] = 0;
+  auto issue_tile = [&](int s, long long t) {  // MODE 3, thread 0 only
+    if (t < ntiles) {
+      long long r0 = t * tr;
+      long long nr = (r0 + tr <= rows ? tr : rows - r0);
+      unsigned bytes = (MODE == 1) ? 0u : (unsigned)(nr * dn * 4);
+      long long a0 = (r0 * RN) & ~3LL, a1 = ((r0 + nr) * RN + 3) & ~3LL;
+      unsigned tbytes = (unsigned)((a1 - a0) * 4);
+      tile_of[s] = t;
+      mbar_expect_tx(&full[s], bytes + tbytes);
+      if (bytes) bulk_g2s_stream(ring + (size_t)s * stage_f4, X + r0 * dn, bytes, &full[s]);
+      bulk_g2s(tring + (size_t)s * tstage, T + a0, tbytes, &full[s]);
+    } else {
+      tile_of[s] = -1;
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[s])) : "memory");
+    }
+#pragma unroll
+    for (int s2 = 0; s2 < kStages; ++s2) issued[s2] += (s2 == s) ? 1 : 0;
+  };
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int s = 0; s < kStages; ++s) {
-      long long t = my_first + (long long)s * gridDim.x;
-      if (t < ntiles) {
+      const long long t = (long long)blockIdx.x + (long long)s * gridDim.x;
+      if (MODE == 3) {
+        issue_tile(s, t);
+      } else if (t < ntiles) {
         long long r0 = t * tr;
         long long nr = (r0 + tr <= rows ? tr : rows - r0);
         unsigned bytes = (MODE == 1) ? 0u : (unsigned)(nr * dn * 4);
@@ -311,10 +338,27 @@ __global__ void __launch_bounds__(1024, 1) k_dense_tma(Geom g, Bufs b, int tr, i
   }
   float res = 0.f;
   unsigned nnz = 0u, inb = 0u;
+  const long long stride = (long long)kStages * gridDim.x;
+  // MODE 3: thread 0 keeps the next two tiles of the counter in hand, fetched two refills ahead
+  // (the atomic's round trip under full HBM load). Tiles are issued in the order they were
+  // fetched, so any left over at the end lie past the last tile.
+  constexpr bool kDyn = (MODE == 3);
+  long long tq0 = -1, tq1 = -1;
+  if (kDyn && threadIdx.x == 0) {
+    tq0 = stride + (long long)atomicAdd(b.ticket + TK_DTILE, 1u);
+    tq1 = stride + (long long)atomicAdd(b.ticket + TK_DTILE, 1u);
+  }
   int it = 0;
-  for (long long t = my_first; t < ntiles; t += gridDim.x, ++it) {
+  // static modes: tile t = CTA + it grid, known before the wait; MODE 3 reads it from the stage
+  for (long long t = blockIdx.x; kDyn || t < ntiles; t += gridDim.x, ++it) {
     const int s = it % kStages;
     const unsigned par = (unsigned)((it / kStages) & 1);
+    long long tnext = -1;
+    if (kDyn && threadIdx.x == 0) {  // every iteration of MODE 3 refills a stage
+      tnext = tq0;
+      tq0 = tq1;
+      tq1 = stride + (long long)atomicAdd(b.ticket + TK_DTILE, 1u);
+    }
     if (!mbar_wait_bounded(&full[s], par)) {
       abort_flag = 1;
     } else if (threadIdx.x == 0) {
@@ -323,6 +367,10 @@ __global__ void __launch_bounds__(1024, 1) k_dense_tma(Geom g, Bufs b, int tr, i
     }
     __syncthreads();
     if (abort_flag) break;
+    if (kDyn) {
+      t = tile_of[s];
+      if (t < 0) break;  // the same value for every thread
+    }
     const long long r0 = t * tr;
     const int nr = (int)(r0 + tr <= rows ? tr : rows - r0);
     if (MODE == 3 || c4 < n4) {  // MODE 3: whole warps, for the ballots of the compressed rows
@@ -362,22 +410,8 @@ __global__ void __launch_bounds__(1024, 1) k_dense_tma(Geom g, Bufs b, int tr, i
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // stage writes -> bulk store
     __syncthreads();  // stage s fully consumed and holding the output rows
-    if (MODE == 3) {  // the stage is read: refill it with the tile kStages ahead
-      if (threadIdx.x == 0) {
-        const long long tn = t + (long long)kStages * gridDim.x;
-        if (tn < ntiles) {
-          long long rn0 = tn * tr;
-          long long nr2 = (rn0 + tr <= rows ? tr : rows - rn0);
-          unsigned bytes = (unsigned)(nr2 * dn * 4);
-          long long a0 = (rn0 * RN) & ~3LL, a1 = ((rn0 + nr2) * RN + 3) & ~3LL;
-          unsigned tbytes = (unsigned)((a1 - a0) * 4);
-          mbar_expect_tx(&full[s], bytes + tbytes);
-          bulk_g2s_stream(ring + (size_t)s * stage_f4, X + rn0 * dn, bytes, &full[s]);
-          bulk_g2s(tring + (size_t)s * tstage, T + a0, tbytes, &full[s]);
-#pragma unroll
-          for (int s2 = 0; s2 < kStages; ++s2) issued[s2] += (s2 == s) ? 1 : 0;
-        }
-      }
+    if (MODE == 3) {  // the stage is read: refill it
+      if (threadIdx.x == 0) issue_tile(s, kDyn ? tnext : t + stride);
     } else if (threadIdx.x == 0) {
       // the tile's output rows leave in one bulk copy; the stage of the previous tile, whose
       // store has now read it, is refilled with the tile kStages ahead of that one
@@ -440,6 +474,7 @@ __global__ void __launch_bounds__(1024, 1) k_dense_tma(Geom g, Bufs b, int tr, i
       }
     }
     if (threadIdx.x == 0) {
+      if (MODE == 3) b.ticket[TK_DTILE] = 0u;  // every CTA has taken its last tile
       b.ticket[TK_DENSE] = 0u;
     }
   }

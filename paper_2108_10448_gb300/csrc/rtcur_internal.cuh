@@ -208,7 +208,7 @@ inline cudaError_t raise_smem_limit(const void* f, size_t bytes) {
   return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-enum { TK_SAMPLE = 0, TK_ERR = 1, TK_DENSE = 2, TK_MAXABS = 3, TK_COUNT = 8 };
+enum { TK_SAMPLE = 0, TK_ERR = 1, TK_DENSE = 2, TK_MAXABS = 3, TK_DTILE = 4, TK_COUNT = 8 };
 
 // ---------------------------------------------------------------- host launch wrappers
 // Every wrapper launches on `s` and returns the launch error.

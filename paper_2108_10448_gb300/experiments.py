@@ -125,7 +125,7 @@ def runtime_vs_d(ds=(100, 200, 300, 400, 500, 600, 700, 800), r=3, alpha=0.1, up
         dims = (d, d, d)
         m, q = synth.sample_sizes(dims, (r, r, r), upsilon)
         for var in variants:
-            times, iters, errs = [], [], []
+            times, iters, errs, conv = [], [], [], 0
             for t in range(trials):
                 X, Lstar, z0 = tucker_problem_gpu(d, r, alpha, seed * 1000003 + d * 31 + t, dev)
                 idx = synth.pack_index_sets(synth.draw_index_sets(dims, m, q, seed=seed + d + t,
@@ -148,11 +148,12 @@ def runtime_vs_d(ds=(100, 200, 300, 400, 500, 600, 700, 800), r=3, alpha=0.1, up
                     rt.rtcur_destroy(plan)
                 times.append(e0.elapsed_time(e1))
                 iters.append(int(res.iters))
+                conv += int(res.status == rt.OK)
                 errs.append(_rel_err(L, Lstar))
                 del X, Lstar, L
             row = {"d": d, "variant": var, "m": m[0], "q": q[0], "ms_mean": float(np.mean(times)),
                    "ms_median": float(np.median(times)), "iters_median": float(np.median(iters)),
-                   "rel_err_median": float(np.median(errs)), "rel_err_max": float(np.max(errs))}
+                   "converged": conv, "rel_err_median": float(np.median(errs)), "rel_err_max": float(np.max(errs))}
             out["rows"].append(row)
             if log:
                 log(json.dumps(row))
