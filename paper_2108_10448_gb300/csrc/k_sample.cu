@@ -9,11 +9,13 @@
 //
 // Reductions are deterministic: per-block partials in a fixed slot, then the last block to
 // finish sums them in block order.
+#include "../../include/rtcur.h"
 #include "rtcur_internal.cuh"
 
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kHtBlocksFull = 2 * 152;
 constexpr int kMaxRedBlocks = 1024;
 
 __device__ __forceinline__ const long long* current_set(const Geom& g, const Bufs& b, int k) {
@@ -317,7 +319,12 @@ cudaError_t launch_gather_x(const Geom& g, const Bufs& b, cudaStream_t s) {
 }
 
 cudaError_t launch_sample_ht(const Geom& g, const Bufs& b, cudaStream_t s) {
-  k_sample_ht<<<grid_for(g.nS), kThreads, 0, s>>>(g, b);
+  // In the FULL scope the dense pass starts beside this kernel: at most kHtBlocksFull blocks (two
+  // per SM of 256 threads x 64 registers) leave every SM room for one of its persistent CTAs,
+  // which would otherwise wait for this kernel's blocks to drain (~30 us per iteration).
+  int grid = grid_for(g.nS);
+  if (g.scope == RTCUR_SCOPE_FULL && grid > kHtBlocksFull) grid = kHtBlocksFull;
+  k_sample_ht<<<grid, kThreads, 0, s>>>(g, b);
   return cudaGetLastError();
 }
 
