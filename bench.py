@@ -34,8 +34,8 @@ METRIC = "RTCUR iters/s & time-to-1e-5 at 800³ rank 5: BF16/TF32 vs FP32 plain,
 # 400^3 pass (dram__bytes_read.sum 259.3 MB + dram__bytes_write.sum 194.9 MB) scaled by the
 # element count to 800^3. The write counter undercounts: up to the L2 size of S is still dirty in
 # L2 when the captured launch ends. Must be dropped whenever the kernel changes.
-DENSE_TRAFFIC = {(800, 800, 800): (259.286272e6 + 194.920192e6) * 8.0,
-                 (400, 400, 400): 259.286272e6 + 194.920192e6}
+DENSE_TRAFFIC = {(800, 800, 800): (259.335680e6 + 195.482624e6) * 8.0,
+                 (400, 400, 400): 259.335680e6 + 195.482624e6}
 DENSE_TRAFFIC_SOURCE = ("ncu --set full of k_dense_tma<5,0> at 400^3 (one launch), "
                         "scaled by elements to the timed size")
 
