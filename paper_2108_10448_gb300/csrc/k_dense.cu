@@ -290,9 +290,9 @@ __global__ void __launch_bounds__(1024, 1) k_dense_tma(Geom g, Bufs b, int tr, i
   // Tiles: the first kStages x grid go out statically (stage s of CTA c holds tile c + s grid).
   // The compressed pass (MODE 3, ~3.7 us a tile) then hands out the rest from a counter, so CTAs
   // that share their SM with the sampled chain's blocks take fewer tiles (1.73 -> 1.67 ms at
-  // 800^3). The other modes keep the static stride: at ~1.5 us a tile the counter's atomics,
-  // all on one L2 slice that every bulk copy also crosses, slowed the dense pass from 0.683 to
-  // 0.85 ms.
+  // 800^3). The other modes keep the static stride in a counted loop: the dense pass with tiles
+  // from the counter ran at 0.84-0.85 ms against 0.67 ms, with one tile per atomic and equally
+  // with 8 or 16, so the cost is the uncounted loop, not the atomics.
   // Thread 0 alone issues copies and counts, per stage, the copies issued and the completions it
   // has observed (for the bounded drain). In MODE 3 a stage past the last tile gets tile -1 and a
   // plain arrive instead of a copy.
