@@ -23,7 +23,8 @@ from dataclasses import dataclass, field
 import numpy as np
 
 __all__ = [
-    "sample_sizes", "draw_index_set", "draw_index_sets", "pack_index_sets",
+    "sample_sizes", "draw_index_set", "draw_index_sets", "draw_chidori_set", "draw_chidori_sets",
+    "pack_index_sets",
     "tucker_lowrank", "planted_outliers", "make_tucker_problem", "make_video_problem",
     "make_batched_problems", "Problem",
 ]
@@ -59,6 +60,31 @@ def draw_index_set(dims, m, q, rng):
         I.append(np.sort(rng.choice(int(dims[i]), size=int(m[i]), replace=False)).astype(np.int64))
         J.append(np.sort(rng.choice(other, size=int(q[i]), replace=False)).astype(np.int64))
     return {"I": I, "J": J}
+
+
+def draw_chidori_set(dims, m, rng):
+    """One draw for the Chidori form of the tensor CUR (the other named form of Sec. 2.2, defined in
+    Cai, Hamm, Huang, Needell, "Mode-wise tensor decompositions"): I_i uniform as above, and J_i
+    every column of X_(i) whose other-mode indices all lie in their I_j, i.e. the fibers through
+    the core subtensor R = X(I_1, ..., I_n). Then |J_i| = prod_{j != i} m_j and C_i(I_i, :) is the
+    mode-i unfolding of R. Column indices follow the same order (row-major over the remaining
+    modes, last fastest), so J_i comes out sorted."""
+    n = len(dims)
+    I = [np.sort(rng.choice(int(dims[i]), size=int(m[i]), replace=False)).astype(np.int64) for i in range(n)]
+    J = []
+    for i in range(n):
+        col = np.zeros(1, dtype=np.int64)
+        for j in range(n):
+            if j != i:
+                col = (col[:, None] * int(dims[j]) + I[j][None, :]).reshape(-1)
+        J.append(col)
+    return {"I": I, "J": J}
+
+
+def draw_chidori_sets(dims, m, seed, n_sets=1):
+    """``n_sets`` independent Chidori draws from one seeded stream (see ``draw_chidori_set``)."""
+    rng = np.random.default_rng([int(seed), 0xC41D])
+    return [draw_chidori_set(dims, m, rng) for _ in range(n_sets)]
 
 
 def draw_index_sets(dims, m, q, seed, n_sets=1):

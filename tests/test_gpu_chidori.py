@@ -1,0 +1,53 @@
+"""The Chidori form of the tensor CUR on the CUDA path (GPU only): index sets whose fibers are
+J_i = prod_{j != i} I_j (every fiber through the core subtensor R, so U_i = R_(i)), passed
+through the same C ABI as the fiber form, against the FP64 oracle on the same sets. Both
+variants, 3 and 4 modes; tolerances as in the main parity tests."""
+import numpy as np
+import pytest
+
+from oracle import rtcur_oracle as O
+from paper_2108_10448_gb300 import rtcur as rt
+from paper_2108_10448_gb300 import synth
+
+from gpu_helpers import rel_fro, run_gpu, support_mismatch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as ge
+    ge.build()
+
+
+CASES = [
+    # dims, ranks, m, alpha, variant, scope
+    ((40, 36, 44), (2, 2, 2), (12, 12, 12), 0.1, "F", rt.SCOPE_SAMPLED),
+    ((40, 36, 44), (2, 2, 2), (12, 12, 12), 0.1, "R", rt.SCOPE_FULL),
+    ((60, 48, 52), (3, 3, 3), (20, 18, 16), 0.15, "F", rt.SCOPE_FULL),
+    ((16, 14, 12, 20), (2, 2, 2, 2), (8, 7, 6, 8), 0.1, "F", rt.SCOPE_SAMPLED),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{'x'.join(map(str, c[0]))}-{c[4]}")
+def test_chidori_sets_match_oracle(case):
+    dims, ranks, m, alpha, variant, scope = case
+    max_iter = 60
+    p = synth.make_tucker_problem(dims, ranks, alpha, 3.0, seed=51, max_iter=max_iter)
+    p.m = list(m)
+    sets = synth.draw_chidori_sets(dims, m, seed=51, n_sets=max_iter if variant == "R" else 1)
+    p.q = [int(s.size) for s in sets[0]["J"]]
+    ref = O.rtcur(p.X, p.ranks, sets, p.zeta0, p.gamma, p.tol, max_iter, variant, keep_full=True)
+    res, L, S = run_gpu(p, sets, variant, scope=scope, max_iter=max_iter)
+    assert res.iters == ref["iters"] > 0
+    np.testing.assert_allclose(res.e_hist[:res.iters], ref["hist"]["e"], rtol=1e-4, atol=2e-7)
+    assert rel_fro(L, ref["L"]) <= 1e-5
+    assert rel_fro(ref["L"], p.L_star) <= 1e-3  # the planted low-rank part is recovered
+    if scope == rt.SCOPE_FULL:
+        inb, outb = support_mismatch(S, ref, p.X)
+        if outb:  # only where the FP32 evaluation of L^(k-1) explains the flip
+            _, Lprev, _ = run_gpu(p, sets, variant, scope=scope, max_iter=ref["iters"] - 1, want_S=False)
+            Lor = ref["prev_state"].full(p.dims)
+            dist = np.abs(np.abs(p.X.astype(np.float64) - Lor) - ref["zeta"])
+            diff = (S != 0) != (ref["S"] != 0)
+            assert int(np.count_nonzero(diff & (dist > 1e-6 * ref["zeta"] + np.abs(Lprev - Lor)))) == 0

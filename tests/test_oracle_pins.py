@@ -344,3 +344,46 @@ def test_sample_sizes_golden():
     for d1, d2, d3, r, v, m, q in rows:
         mm, qq = synth.sample_sizes((d1, d2, d3), (r, r, r), v)
         assert mm == [m] * 3 and qq == [q] * 3
+
+
+# --------------------------------------------------------------------------- Chidori form
+def test_chidori_sets_give_u_equal_to_unfolded_core():
+    # Chidori CUR: J_i = prod_{j != i} I_j, so C_i(I_i, :) is the mode-i unfolding of R (brute force)
+    rng = _rng(21)
+    for dims, m in (((7, 6, 5), (3, 2, 4)), ((5, 4, 6, 3), (2, 3, 2, 2))):
+        X = rng.standard_normal(dims)
+        sets = synth.draw_chidori_set(dims, m, rng)
+        R = O.gather_subtensor(X, sets["I"])
+        for i in range(len(dims)):
+            assert np.all(np.diff(sets["J"][i]) > 0) and sets["J"][i].size == np.prod(m) // m[i]
+            C = O.gather_fibers(X, i, sets["J"][i])
+            np.testing.assert_array_equal(C[sets["I"][i]], O.unfold(R, i))
+            # every fiber passes through the core: its other-mode indices lie in their I_j
+            for col, jj in enumerate(sets["J"][i][:5]):
+                coords = np.unravel_index(jj, [d for k, d in enumerate(dims) if k != i])
+                others = [sets["I"][k] for k in range(len(dims)) if k != i]
+                assert all(c in o for c, o in zip(coords, others))
+
+
+@pytest.mark.parametrize("dims,ranks", [((9, 8, 10), (2, 3, 2)), ((6, 5, 4, 7), (2, 2, 3, 2))])
+def test_chidori_cur_exact_reconstruction(dims, ranks):
+    # rank(U_i) = r_i with the Chidori fibers  =>  R x_i (C_i U_i^+) reproduces the tensor
+    A_t = _exact_tucker(dims, ranks, 22)
+    rng = _rng(23)
+    m = [min(d, r + 2) for d, r in zip(dims, ranks)]
+    sets = synth.draw_chidori_set(dims, m, rng)
+    R = O.gather_subtensor(A_t, sets["I"])
+    C = [O.gather_fibers(A_t, i, sets["J"][i]) for i in range(len(dims))]
+    L = O.tucker_full(R, O.fiber_cur(R, C, sets["I"], ranks))
+    assert np.linalg.norm(L - A_t) / np.linalg.norm(A_t) <= 1e-12
+
+
+def test_chidori_recovery_of_planted_low_rank():
+    # Sec. 4.1 success criterion with Chidori sampling at low outlier density
+    p = synth.make_tucker_problem((30, 30, 30), (2, 2, 2), 0.05, 3.0, seed=24, outlier_scale=1.0,
+                                  dtype=np.float64)
+    m = [15, 15, 15]
+    sets = synth.draw_chidori_sets(p.dims, m, seed=24)
+    out = O.rtcur(p.X, p.ranks, sets, float(np.max(np.abs(p.L_star))), 0.7, 1e-5, 100, "F")
+    L = out["state"].full(p.dims)
+    assert np.linalg.norm(L - p.L_star) / np.linalg.norm(p.L_star) <= 1e-3
