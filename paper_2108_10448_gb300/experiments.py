@@ -56,15 +56,22 @@ def _rel_err(L, Ls):
 
 def phase_transition(d=300, ranks=(3, 5, 10), alphas=(0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7),
                      upsilons=(1, 2, 3, 4, 5), trials=10, variants=("F", "R"), seed=0, max_iter=100,
-                     log=None):
-    """Success counts per (variant, r, upsilon, alpha). Cells whose |I_i| exceeds the library's
-    limit are reported as unsupported."""
+                     sampling="fiber", log=None):
+    """Success counts per (variant, r, upsilon, alpha). sampling = "fiber" draws J_i uniformly
+    (|J_i| = ceil(v r ln d^2)); "chidori" takes J_i = prod_{j != i} I_j (|J_i| = |I|^2). Cells
+    whose sample sizes exceed the library's limits are reported as unsupported."""
     import torch
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream().cuda_stream
     dims = (d, d, d)
-    out = {"d": d, "trials": trials, "alphas": list(alphas), "cells": []}
+    out = {"d": d, "trials": trials, "alphas": list(alphas), "sampling": sampling, "cells": []}
     t0 = time.time()
+
+    def draw(m, q, sd, n_sets):
+        if sampling == "chidori":
+            return synth.draw_chidori_sets(dims, m, seed=sd, n_sets=n_sets)
+        return synth.draw_index_sets(dims, m, q, seed=sd, n_sets=n_sets)
+
     for r in ranks:
         # the problems of one (r, alpha) serve every upsilon and variant
         probs = {}
@@ -74,6 +81,8 @@ def phase_transition(d=300, ranks=(3, 5, 10), alphas=(0.1, 0.2, 0.3, 0.4, 0.5, 0
         Ls = [torch.empty((d, d, d), device=dev, dtype=torch.float32) for _ in range(trials)]
         for ups in upsilons:
             m, q = synth.sample_sizes(dims, (r, r, r), ups)
+            if sampling == "chidori":
+                q = [m[1] * m[2], m[0] * m[2], m[0] * m[1]]
             for var in variants:
                 cell_base = {"variant": var, "r": r, "upsilon": ups, "m": m[0], "q": q[0]}
                 vcode = rt.VARIANT_R if var == "R" else rt.VARIANT_F
@@ -90,9 +99,8 @@ def phase_transition(d=300, ranks=(3, 5, 10), alphas=(0.1, 0.2, 0.3, 0.4, 0.5, 0
                         out["cells"].append(dict(cell_base, alpha=a, unsupported=str(exc)))
                         continue
                     try:
-                        idxs = [synth.pack_index_sets(synth.draw_index_sets(
-                            dims, m, q, seed=seed * 7 + r * 131 + int(ups * 17) + ai * 3 + t,
-                            n_sets=max_iter if var == "R" else 1)) for t in range(trials)]
+                        idxs = [synth.pack_index_sets(draw(m, q, seed * 7 + r * 131 + int(ups * 17) + ai * 3 + t,
+                                                           max_iter if var == "R" else 1)) for t in range(trials)]
                         res = rt.rtcur_solve_batched(plans, [p[0].data_ptr() for p in probs[a]], idxs,
                                                      L_ptrs=[L.data_ptr() for L in Ls], stream=stream,
                                                      max_iter=max_iter)
@@ -171,6 +179,7 @@ def main():
     ap.add_argument("--alphas", default="0.1,0.2,0.3,0.4,0.5,0.6,0.7")
     ap.add_argument("--upsilons", default="1,2,3,4,5")
     ap.add_argument("--ds", default="100,200,300,400,500,600,700,800")
+    ap.add_argument("--sampling", default="fiber", choices=["fiber", "chidori"])
     a = ap.parse_args()
     import __graft_entry__ as ge  # builds the library if needed
     ge.build()
@@ -182,7 +191,8 @@ def main():
     if a.which == "phase":
         res = phase_transition(d=a.d, ranks=[int(x) for x in a.ranks.split(",")],
                                alphas=[float(x) for x in a.alphas.split(",")],
-                               upsilons=[float(x) for x in a.upsilons.split(",")], trials=a.trials, log=log)
+                               upsilons=[float(x) for x in a.upsilons.split(",")], trials=a.trials,
+                               sampling=a.sampling, log=log)
     else:
         res = runtime_vs_d(ds=[int(x) for x in a.ds.split(",")], trials=a.trials, log=log)
     with open(a.out, "w") as f:
