@@ -16,7 +16,7 @@ sampled value entering R and C_i is
 so X receives the adjoint of the unmasked slots and L^(k) (the previous iteration's factors)
 that of the masked ones.
 
-Readings (also listed in the design doc):
+Readings:
   * the truncated pseudoinverse is differentiated where rank(U_i) >= r_i and sigma_{r_i} >
     sigma_{r_i + 1} (a.e.); the SVD_r cutoff is not active there;
   * U_i^+ = W^T Z with W = C_i(I_i,:), Z = sum_{j<=r} lambda_j^-1 u_j u_j^T over the top r

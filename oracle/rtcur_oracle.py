@@ -15,7 +15,7 @@ Every function follows one passage of the paper:
   * stopping error e^(k)                 -- Sec. 3.3, Eq. (rel_err)
   * RTCUR-F / RTCUR-R                    -- Sec. 3.4, Algorithm 1
 
-Readings where the paper is silent (each also listed in the design doc):
+Readings where the paper is silent:
   * indices are 0-based; J_i indexes columns of X_(i) in row-major order of the remaining
     modes (last mode fastest); sets are sorted (order does not change L);
   * zeta decays before the first thresholding (Algorithm 1 order), so S^(1) = HT_{gamma zeta0}(X);
