@@ -87,3 +87,23 @@ def test_s_format_options_are_validated(lib):
             rt.rtcur_create(dims, [2, 2, 2], [4, 4, 4], [8, 8, 8], 1.0, 0.7, 1e-5, 5, 0, rt.make_options(**kw))
         assert ei.value.status == rt.EINVAL
         assert msg in str(ei.value)
+
+
+def test_compressed_s_geometry_is_validated(lib):
+    from paper_2108_10448_gb300 import rtcur as rt
+    o = rt.make_options(scope=rt.SCOPE_FULL, s_format=rt.S_COMPRESSED)
+    for dims, ranks, nI, nJ in (([4, 4, 4100], [2, 2, 2], [4, 4, 4], [8, 8, 8]),   # d_n > 4096
+                                ([20, 20, 40], [2, 2, 9], [4, 4, 12], [8, 8, 20])):  # r_n > 8
+        with pytest.raises(rt.RTCURError) as ei:
+            rt.rtcur_create(dims, ranks, nI, nJ, 1.0, 0.7, 1e-5, 5, 0, o)
+        assert ei.value.status == rt.EINVAL
+        assert "s_format COMPRESSED needs d_n % 4 == 0" in str(ei.value)
+
+
+def test_compressed_s_calls_reject_a_null_plan(lib):
+    import ctypes as C
+    from paper_2108_10448_gb300 import rtcur as rt
+    out = rt.rtcur_s_compressed()
+    assert lib.rtcur_get_s_compressed(None, C.byref(out), None) == rt.EINVAL
+    assert lib.rtcur_compact_s(None, None, None, None) == rt.EINVAL
+    assert lib.rtcur_decode_s(None, None, None) == rt.EINVAL
