@@ -107,3 +107,34 @@ def test_compressed_s_calls_reject_a_null_plan(lib):
     assert lib.rtcur_get_s_compressed(None, C.byref(out), None) == rt.EINVAL
     assert lib.rtcur_compact_s(None, None, None, None) == rt.EINVAL
     assert lib.rtcur_decode_s(None, None, None) == rt.EINVAL
+
+
+def test_header_compiles_as_c_and_matches_the_binding(tmp_path):
+    # the boundary is plain C: the header compiles as C99, and its structs have the layout the
+    # ctypes binding declares (sizes and field offsets)
+    import ctypes as C
+    import shutil
+    import subprocess
+    from paper_2108_10448_gb300 import rtcur as rt
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"rtcur_options": rt.rtcur_options, "rtcur_result": rt.rtcur_result,
+               "rtcur_s_compressed": rt.rtcur_s_compressed}
+    lines = ['#include "rtcur.h"', "#include <stddef.h>", "#include <stdio.h>", "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "abi.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "abi"
+    subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                  text=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == C.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert int(got[f"{name}.{f}"]) == getattr(cls, f).offset, f"{name}.{f}"
