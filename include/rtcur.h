@@ -159,7 +159,9 @@ RTCUR_API rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int
  *          (iteration k uses set k)
  *   L_out  device, prod d_i floats or NULL: receives L^(k) = R x_i (C_i U_i^+) (Eq. L=CUR)
  *   S_out  device, prod d_i floats or NULL: receives S^(k) = HT_{zeta^(k)}(X - L^(k-1)) over
- *          the whole tensor (in the FULL scope it is also the buffer written every iteration)
+ *          the whole tensor (in the FULL scope with s_format DENSE it is also the buffer
+ *          written every iteration; with COMPRESSED it is filled once, by expanding the
+ *          compressed S^(k), see rtcur_get_s_compressed)
  *   res    host, filled on return (may be NULL)
  * The loop runs on the device as one CUDA graph with a conditional WHILE node; the host
  * synchronises once at the end. Returns RTCUR_OK or RTCUR_NOT_CONVERGED on success. */
@@ -179,7 +181,8 @@ RTCUR_API rtcur_status rtcur_finish(rtcur_plan* plan, float* L_out, float* S_out
 /* rtcur_threshold_dense -- Step (I) of Algorithm 1 over the whole tensor for the current state:
  * S_work = HT_{gamma zeta^(k)}(X - L^(k)) (Eq. S=HT(X-L)) with the plan's dense form, n_launch
  * times (identical launches; for timing the fused pass alone). Needs a FULL-scope plan after
- * rtcur_begin; writes the S_work buffer given to rtcur_begin and the dense counters that
+ * rtcur_begin; writes the S_work buffer given to rtcur_begin (with s_format COMPRESSED the
+ * plan's compressed S instead; S_work is then unused) and the dense counters that
  * rtcur_finish reports. Does not advance k. No host sync. */
 RTCUR_API rtcur_status rtcur_threshold_dense(rtcur_plan* plan, int32_t n_launch, void* stream);
 
