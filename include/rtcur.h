@@ -24,8 +24,12 @@
  *     that return results on the host synchronise `stream` once before returning.
  *   - No call throws. Every call returns an rtcur_status. Invalid arguments return
  *     RTCUR_EINVAL before any GPU work; the message is kept per plan (rtcur_last_error).
- *   - A plan owns all device workspace, sized at rtcur_create; the solve calls allocate
- *     nothing. A plan is not thread-safe; distinct plans are independent.
+ *   - A plan owns all device workspace, sized at rtcur_create; rtcur_solve, rtcur_begin /
+ *     rtcur_iterate / rtcur_finish, rtcur_backward and the export calls allocate nothing. The one
+ *     exception is rtcur_solve_batched: the first call for a new list of plans builds and caches
+ *     a batch graph, which allocates a small device array (one pointer per plan) and the graph's
+ *     own resources; later calls with the same list allocate nothing. A plan is not thread-safe;
+ *     distinct plans are independent.
  */
 #ifndef RTCUR_H
 #define RTCUR_H
@@ -197,7 +201,9 @@ RTCUR_API rtcur_status rtcur_threshold_dense(rtcur_plan* plan, int32_t n_launch,
  *   X      device, prod d_i floats, 16-byte aligned;  S  device output, prod d_i floats, 16-byte aligned
  *   zeta   threshold used as given (HT keeps |x - L| > zeta, compared in FP32)
  *   counts host double[3] or NULL: {||X - L - S||_F^2, nnz(S), band count}; when given, the call
- *          synchronises `stream`
+ *          synchronises `stream` and returns a device-side error of the pass (RTCUR_ETIMEOUT when a
+ *          bounded wait gave up and S may be incomplete); with NULL the call does not synchronise
+ *          and such an error is not reported
  * Scratch: one fixed 32 MiB device array inside the library (held by every GPU that loads it
  * until the process exits); problems needing more (prod_{i<n} d_i * r_n + 4 floats of table plus
  * ~1.1 MB) return RTCUR_EINVAL. Nothing is allocated: no cudaMalloc, no cudaFree. The first call
@@ -241,7 +247,24 @@ RTCUR_API rtcur_status rtcur_decode_s(rtcur_plan* plan, float* S_out, void* stre
 RTCUR_API rtcur_status rtcur_get_factors(rtcur_plan* plan, float* G, float* B, int32_t* k, double* zeta,
                                void* stream);
 
-/* Sizes of the plan's sampled-entry buffer and of its segments, for callers that read it. */
+/* rtcur_get_cur -- copy Algorithm 1's output of the current iterate, the Fiber CUR pieces
+ * (R, C_i, U_i^+) with L^(k) = R x_1 (C_1 U_1^+) x_2 ... x_n (C_n U_n^+) (Eq. (L=CUR), Eq. (R, C_i,
+ * U_i) of Sec. 3.1), to host arrays. They are the pieces of the last iteration k: formed from
+ * X - S^(k) on that iteration's index sets (set 0 for variant F, set (k - 1) mod max_iter for
+ * variant R), in the order of those sets.
+ *   R      host, prod |I_i| floats or NULL: R = (X - S^(k))(I_1, ..., I_n), row-major
+ *   C      host, sum_i d_i |J_i| floats or NULL: C_i = (X - S^(k))_(i)(:, J_i), d_i x |J_i|
+ *          row-major, packed mode after mode
+ *   Upinv  host, sum_i |J_i| |I_i| doubles or NULL: U_i^+ = (SVD_{r_i}(C_i(I_i, :)))^+ in FP64,
+ *          |J_i| x |I_i| row-major, packed mode after mode (rank r_i, or fewer where the SVD_r
+ *          cutoff dropped singular values: RTCUR_FLAG_RANK_DEFICIENT)
+ *   k      host or NULL: receives the iteration count k
+ * The staging buffers are plan workspace (no allocation). Synchronises `stream`.
+ * Errors: RTCUR_EINVAL (NULL plan, no rtcur_begin, or k = 0: L^(0) = 0 has no CUR pieces),
+ * RTCUR_ECUDA. */
+RTCUR_API rtcur_status rtcur_get_cur(rtcur_plan* plan, float* R, float* C, double* Upinv, int32_t* k,
+                                     void* stream);
+
 /* Batched form: `count` independent problems (each with its own plan, so dims, ranks, sample
  * sizes, variant and tolerance may all differ) solved together by ONE graph launch. The graph is
  * a device-side WHILE loop whose body holds, per problem, a conditional IF node around that
@@ -273,6 +296,22 @@ RTCUR_API rtcur_status rtcur_solve_batched(rtcur_plan* const* plans, int32_t cou
  * create; allocates nothing. */
 RTCUR_API rtcur_status rtcur_backward(rtcur_plan* plan, const float* dL, float* dX, void* stream);
 
+/* rtcur_set_wait_limit -- bound on the device-side waits of the plan's FP32 dense threshold pass
+ * (the FULL scope's per-iteration pass over the whole tensor, Eq. S=HT(X-L)). Each tile of that
+ * pass waits for its asynchronous copy on a shared-memory barrier; a wait that does not complete
+ * within its bound gives up, the pass waits (with the default bound) for its own copies still in
+ * flight, records RTCUR_ETIMEOUT and returns, the solve stops after the iteration and
+ * rtcur_finish / rtcur_solve return RTCUR_ETIMEOUT. The context stays usable and the next
+ * rtcur_begin clears the error.
+ *   polls  0: the default bound (2^26 polls, seconds); n > 0: n non-blocking polls per wait, from
+ *          the next launch on (a short bound reports a stalled pass sooner; 1 makes the first
+ *          wait of every launch give up, which is how the failure path is tested)
+ * The paper has no counterpart (failure detection of the pass). Synchronises `stream`.
+ * Errors: RTCUR_EINVAL (NULL plan, polls < 0), RTCUR_ECUDA. */
+RTCUR_API rtcur_status rtcur_set_wait_limit(rtcur_plan* plan, int64_t polls, void* stream);
+
+/* Number of sampled entries per iteration: prod |I_i| + sum_i d_i |J_i| (the subtensor R and the
+ * n fiber sets C_i of Sec. 3.3). 0 for a NULL plan. */
 RTCUR_API int64_t rtcur_sample_count(const rtcur_plan* plan);
 
 /* Last error message of a plan (NULL plan: the last create failure); never NULL. */

@@ -441,6 +441,12 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
   AL(b.e_hist, max_iter);
   AL(b.z_hist, max_iter);
   AL(b.nnz_hist, max_iter);
+  {
+    long long nU = 0;
+    for (int i = 0; i < n_modes; ++i) nU += (long long)g.q[i] * g.m[i];
+    AL(b.curF, g.nS);
+    AL(b.curU, nU);
+  }
 #ifdef RTCUR_TIMELINE
   AL(b.tl, 4096);
   AL(b.tl_n, 1);
@@ -524,6 +530,7 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
     }
   }
   if (e == cudaSuccess) e = cudaMemset(b.ticket, 0, sizeof(unsigned) * TK_COUNT);
+  if (e == cudaSuccess) e = cudaMemset(b.st, 0, sizeof(State));
   if (e != cudaSuccess) {
     rtcur_status st = (e == cudaErrorMemoryAllocation) ? RTCUR_ENOMEM : RTCUR_ECUDA;
     fail(nullptr, st, "allocating the plan: %s", cudaGetErrorString(e));
@@ -768,6 +775,27 @@ rtcur_status rtcur_get_factors(rtcur_plan* p, float* G, float* B, int32_t* k, do
   return RTCUR_OK;
 }
 
+rtcur_status rtcur_get_cur(rtcur_plan* p, float* R, float* C, double* Upinv, int32_t* k,
+                           void* stream) {
+  if (!p) return fail(nullptr, RTCUR_EINVAL, "plan is NULL");
+  if (!p->begun) return fail(p, RTCUR_EINVAL, "rtcur_begin must come first");
+  const Geom& g = p->g;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  State h;
+  CKC(p, cudaMemcpyAsync(&h, p->b.st, sizeof h, cudaMemcpyDeviceToHost, s));
+  CKC(p, cudaStreamSynchronize(s));
+  if (k) *k = h.k;
+  if (h.k < 1) return fail(p, RTCUR_EINVAL, "no iteration has run (L^(0) = 0 has no CUR factors)");
+  long long nU = 0;
+  for (int i = 0; i < g.n; ++i) nU += (long long)g.q[i] * g.m[i];
+  CKC(p, launch_export_cur(g, p->b, s));
+  if (R) CKC(p, cudaMemcpyAsync(R, p->b.curF, sizeof(float) * g.nR, cudaMemcpyDeviceToHost, s));
+  if (C) CKC(p, cudaMemcpyAsync(C, p->b.curF + g.nR, sizeof(float) * (g.nS - g.nR), cudaMemcpyDeviceToHost, s));
+  if (Upinv) CKC(p, cudaMemcpyAsync(Upinv, p->b.curU, sizeof(double) * nU, cudaMemcpyDeviceToHost, s));
+  CKC(p, cudaStreamSynchronize(s));
+  return RTCUR_OK;
+}
+
 rtcur_status rtcur_backward(rtcur_plan* p, const float* dL, float* dX, void* stream) {
   if (!p) return fail(nullptr, RTCUR_EINVAL, "plan is NULL");
   if (!dL || !dX) return fail(p, RTCUR_EINVAL, "dL and dX must not be NULL");
@@ -784,6 +812,16 @@ rtcur_status rtcur_backward(rtcur_plan* p, const float* dL, float* dX, void* str
     return fail(p, RTCUR_EINVAL, "the solve ran %d iterations, more than the %d recorded", h.k, g.ck_iters);
   if (h.err != 0) return fail(p, (rtcur_status)h.err, "the forward pass latched device error %d", h.err);
   CKC(p, launch_backward(g, p->b, p->bw, h.k, dL, dX, s));
+  return RTCUR_OK;
+}
+
+rtcur_status rtcur_set_wait_limit(rtcur_plan* p, int64_t polls, void* stream) {
+  if (!p) return fail(nullptr, RTCUR_EINVAL, "plan is NULL");
+  if (polls < 0) return fail(p, RTCUR_EINVAL, "polls must be >= 0");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  long long v = polls;
+  CKC(p, cudaMemcpyAsync(&p->b.st->wait_polls, &v, sizeof v, cudaMemcpyHostToDevice, s));
+  CKC(p, cudaStreamSynchronize(s));
   return RTCUR_OK;
 }
 

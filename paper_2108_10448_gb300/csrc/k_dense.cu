@@ -185,6 +185,25 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsig
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// The tile loop's wait: the default bound, or `polls` non-blocking tests when the caller set a
+// shorter limit (rtcur_set_wait_limit). The drain after a timeout always keeps the default bound.
+__device__ __forceinline__ bool mbar_wait_tile(unsigned long long* bar, unsigned parity, long long polls) {
+  if (polls <= 0) return mbar_wait_bounded(bar, parity);
+  for (long long i = 0; i < polls; ++i)
+    if (mbar_test(bar, parity)) return true;
+  return false;
+}
 // 1-D bulk copy of streamed data with an L2 evict-first policy: the tensor passes through L2
 // once, so it should not push out the small working set of the concurrent sampled chain.
 __device__ __forceinline__ void bulk_g2s_stream(void* dst, const void* src, unsigned bytes,
@@ -247,6 +266,7 @@ __global__ void __launch_bounds__(1024, 1) k_dense_tma(Geom g, Bufs b, int tr, i
   __shared__ long long tile_of[kStages];     // tile held by each stage, -1: no more tiles
   const State* st = b.st;
   const int kk = st->k;
+  const long long polls = st->wait_polls;
   constexpr bool kFused = (MODE == 0 || MODE == 3);  // the iteration's threshold pass
   const int cur = kFused ? (kk & 1) : ((kk + copy_sel) & 1);
   const double zeta = kFused ? g.gamma * st->zeta : st->zeta;
@@ -359,7 +379,7 @@ __global__ void __launch_bounds__(1024, 1) k_dense_tma(Geom g, Bufs b, int tr, i
       tq0 = tq1;
       tq1 = stride + (long long)atomicAdd(b.ticket + TK_DTILE, 1u);
     }
-    if (!mbar_wait_bounded(&full[s], par)) {
+    if (!mbar_wait_tile(&full[s], par, polls)) {
       abort_flag = 1;
     } else if (threadIdx.x == 0) {
 #pragma unroll

@@ -174,6 +174,47 @@ __global__ void __launch_bounds__(kThreads) k_table_B(Geom g, Bufs b, int next) 
   TL_END(10);
 }
 
+// Algorithm 1's output (R, C_i, U_i^+) of the current L^(k), staged for the host:
+//   curF[0, nR)             R = (X - S^(k))(I_1..I_n), the sample buffer's segment 0 as it is
+//   curF[seg[1+i] + t q_i + j]  C_i(t, j), row-major d_i x q_i (the sample buffer holds it
+//                           fiber-major: entry j d_i + t)
+//   curU[sum_{l<i} q_l m_l + j m_i + a]  U_i^+(j, a) = sum_c Y_i(j, c) Q_{r,i}(a, c), FP64: the
+//                           truncated pseudoinverse V_r Sigma_r^-1 Q_r^T of Eq. (R, C_i, U_i), from
+//                           the factors the pinv stage left (Y_i = W_i^T Q_r Sigma_r^-2, or
+//                           W_i^T X_1 H^-1 with Q_r = X_1 on the certified path: the same product)
+__global__ void __launch_bounds__(kThreads) k_export_cur(Geom g, Bufs b) {
+  long long e = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (e < g.nS) {
+    if (e < g.nR) {
+      b.curF[e] = b.XS[e];
+      return;
+    }
+    int i = 0;
+    while (i + 1 < g.n && e >= g.seg[i + 2]) ++i;
+    const long long local = e - g.seg[i + 1];
+    const long long t = local / g.q[i], j = local - t * g.q[i];
+    b.curF[e] = b.XS[g.seg[i + 1] + j * g.d[i] + t];
+    return;
+  }
+  e -= g.nS;
+  long long off = 0;
+  for (int i = 0; i < g.n; ++i) {
+    const long long sz = (long long)g.q[i] * g.m[i];
+    if (e < off + sz) {
+      const long long local = e - off;
+      const int j = (int)(local / g.m[i]), a = (int)(local - (long long)j * g.m[i]);
+      const int r = g.r[i];
+      const double* Y = b.Y + g.offY[i] + (long long)j * r;
+      const double* Q = b.Qr + g.offQ[i] + (long long)a * r;
+      double acc = 0.0;
+      for (int c = 0; c < r; ++c) acc = fma(Y[c], Q[c], acc);
+      b.curU[e] = acc;
+      return;
+    }
+    off += sz;
+  }
+}
+
 inline int nblocks(long long work) { return (int)((work + kThreads - 1) / kThreads); }
 
 }  // namespace
@@ -206,5 +247,12 @@ cudaError_t launch_table(const Geom& g, const Bufs& b, int next, cudaStream_t s)
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_table_B<<<nblocks(g.rowsT * g.rlast), kThreads, 0, s>>>(g, b, next);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_export_cur(const Geom& g, const Bufs& b, cudaStream_t s) {
+  long long nU = 0;
+  for (int i = 0; i < g.n; ++i) nU += (long long)g.q[i] * g.m[i];
+  k_export_cur<<<nblocks(g.nS + nU), kThreads, 0, s>>>(g, b);
   return cudaGetLastError();
 }

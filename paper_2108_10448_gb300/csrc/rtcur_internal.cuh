@@ -96,6 +96,8 @@ struct State {
   double zeta0;      // max|X| when requested
   int jsweeps;       // FP32 eigensolver sweeps/steps of the last iteration (max over modes)
   long long warm_hits;  // certified warm results, counted over the solve
+  long long wait_polls; // polls of a bounded wait in the dense pass's tile loop (0: the default);
+                        // set by rtcur_set_wait_limit, kept across solves
   int pad;
 };
 
@@ -154,6 +156,10 @@ struct Bufs {
   float* svals;
   long long* srow;   // rowsT + 1
   long long* soff;   // (rowsT + 1) / 1023 + 64
+  // Algorithm 1's output staged for rtcur_get_cur: R and C_i (nS floats, C_i row-major) and
+  // U_i^+ (sum q_i m_i doubles, q_i x m_i row-major)
+  float* curF;
+  double* curU;
 };
 
 // Workspace of the adjoint (rtcur_backward), 3-mode tensors. Per recorded iteration and mode:
@@ -222,6 +228,7 @@ cudaError_t launch_refine(const Geom& g, const Bufs& b, int mode, cudaStream_t s
 cudaError_t launch_factor_B(const Geom& g, const Bufs& b, cudaStream_t s);
 cudaError_t launch_core(const Geom& g, const Bufs& b, cudaStream_t s);
 cudaError_t launch_table(const Geom& g, const Bufs& b, int next, cudaStream_t s);
+cudaError_t launch_export_cur(const Geom& g, const Bufs& b, cudaStream_t s);
 cudaError_t launch_sample_err(const Geom& g, const Bufs& b, cudaStream_t s);
 cudaError_t launch_commit(const Geom& g, const Bufs& b, unsigned long long handle, int use_handle,
                           cudaStream_t s);

@@ -76,9 +76,12 @@ def load(path=LIB_PATH):
     lib.rtcur_threshold_dense_noalloc.restype = C.c_int
     lib.rtcur_get_factors.argtypes = [P, C.POINTER(C.c_float), C.POINTER(C.c_float),
                                       C.POINTER(C.c_int32), C.POINTER(C.c_double), P]
+    lib.rtcur_get_cur.argtypes = [P, C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(C.c_double),
+                                  C.POINTER(C.c_int32), P]
     lib.rtcur_get_s_compressed.argtypes = [P, C.POINTER(rtcur_s_compressed), P]
     lib.rtcur_decode_s.argtypes = [P, P, P]
     lib.rtcur_compact_s.argtypes = [P, P, P, P]
+    lib.rtcur_set_wait_limit.argtypes = [P, C.c_int64, P]
     lib.rtcur_sample_count.argtypes = [P]
     lib.rtcur_sample_count.restype = C.c_int64
     lib.rtcur_last_error.argtypes = [P]
@@ -86,8 +89,8 @@ def load(path=LIB_PATH):
     lib.rtcur_destroy.argtypes = [P]
     lib.rtcur_destroy.restype = None
     for f in ("rtcur_create", "rtcur_solve", "rtcur_begin", "rtcur_iterate", "rtcur_finish",
-              "rtcur_get_factors", "rtcur_threshold_dense", "rtcur_backward", "rtcur_solve_batched",
-              "rtcur_get_s_compressed", "rtcur_decode_s", "rtcur_compact_s"):
+              "rtcur_get_factors", "rtcur_get_cur", "rtcur_threshold_dense", "rtcur_backward", "rtcur_solve_batched",
+              "rtcur_get_s_compressed", "rtcur_decode_s", "rtcur_compact_s", "rtcur_set_wait_limit"):
         getattr(lib, f).restype = C.c_int
     _lib = lib
     return lib
@@ -278,6 +281,33 @@ def rtcur_get_factors(plan, dims, ranks, stream=0):
         Bs.append(B[off:off + d * r].reshape(d, r))
         off += d * r
     return G.reshape(tuple(ranks)), Bs, k.value, z.value
+
+
+def rtcur_get_cur(plan, dims, nI, nJ, stream=0):
+    """Algorithm 1's output for the current iterate: (R, [C_1..C_n], [U_1^+..U_n^+], k) with
+    R (|I_1| x ... x |I_n|, FP32), C_i (d_i x |J_i|, FP32) and U_i^+ (|J_i| x |I_i|, FP64), host
+    arrays, so that L^(k) = R x_i (C_i U_i^+)."""
+    n = len(dims)
+    R = np.zeros(int(np.prod(nI)), np.float32)
+    Cf = np.zeros(int(sum(int(d) * int(q) for d, q in zip(dims, nJ))), np.float32)
+    U = np.zeros(int(sum(int(q) * int(m) for q, m in zip(nJ, nI))), np.float64)
+    k = C.c_int32()
+    _check(load().rtcur_get_cur(plan, R.ctypes.data_as(C.POINTER(C.c_float)),
+                                Cf.ctypes.data_as(C.POINTER(C.c_float)),
+                                U.ctypes.data_as(C.POINTER(C.c_double)), C.byref(k), stream or None), plan)
+    Cs, Us, oc, ou = [], [], 0, 0
+    for i in range(n):
+        d, q, m = int(dims[i]), int(nJ[i]), int(nI[i])
+        Cs.append(Cf[oc:oc + d * q].reshape(d, q))
+        Us.append(U[ou:ou + q * m].reshape(q, m))
+        oc += d * q
+        ou += q * m
+    return R.reshape(tuple(int(m) for m in nI)), Cs, Us, k.value
+
+
+def rtcur_set_wait_limit(plan, polls, stream=0):
+    """Bound (in polls; 0 = default) on the waits of the plan's FP32 dense threshold pass."""
+    _check(load().rtcur_set_wait_limit(plan, int(polls), stream or None), plan, allow=(OK,))
 
 
 def rtcur_sample_count(plan):
