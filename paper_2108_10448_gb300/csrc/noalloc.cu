@@ -12,8 +12,11 @@
 // allocating library routine.
 //
 // The array is shared by every call on a device and keeps the last call's contents; the parts
-// that must start at zero (the reduction tickets) are cleared at each call. Calls whose work
-// overlaps on the GPU (different streams, or different host threads) race on the array.
+// that must start at zero (the reduction tickets) are cleared at each call, by a one-thread-block
+// kernel that also writes the call's state from its arguments (no host staging buffer). Calls
+// whose work overlaps on the GPU (different streams, or different host threads) race on the
+// array. Device-side errors (a bounded wait of the pass that gave up) are read back only when the
+// caller asks for the counts.
 //
 // Host code cannot use the array's name as a device address (in host code the name is a
 // host-side stand-in; a kernel given it would fault or, where the GPU can reach host memory,
@@ -37,6 +40,26 @@ std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Resets the call's device state in the scratch: the loop state (k = 0 so that copy 0 holds the
+// caller's G and B; zeta as given; the dense counters), the pointers to X and S, and the
+// reduction tickets. Everything arrives as kernel arguments, so no host buffer has to outlive the
+// call.
+__global__ void k_noalloc_init(State* st, SolvePtrs* sp, unsigned* ticket, double zeta,
+                               const float* X, float* S) {
+  if (threadIdx.x == 0) {
+    State h;
+    memset(&h, 0, sizeof h);
+    h.zeta = zeta;
+    h.e = 1.0;
+    h.nnz_f = h.inband_f = -1;
+    h.resid_f = -1.0;
+    *st = h;
+    sp->X = X;
+    sp->S = S;
+  }
+  if (threadIdx.x < TK_COUNT) ticket[threadIdx.x] = 0u;
+}
 
 }  // namespace
 
@@ -106,19 +129,8 @@ extern "C" RTCUR_API rtcur_status rtcur_threshold_dense_noalloc(
   b.T[0] = b.T[1] = reinterpret_cast<float*>(base + oT);
   b.G[0] = b.G[1] = const_cast<float*>(G);
   b.B[0] = b.B[1] = const_cast<float*>(B);
-  State h;
-  memset(&h, 0, sizeof h);
-  h.k = 0;  // copy 0 holds the caller's G and B
-  h.zeta = zeta;
-  h.e = 1.0;
-  h.nnz_f = h.inband_f = -1;
-  h.resid_f = -1.0;
-  SolvePtrs sp;
-  sp.X = X;
-  sp.S = S;
-  if (cudaMemcpyAsync(b.st, &h, sizeof h, cudaMemcpyHostToDevice, s) != cudaSuccess) return RTCUR_ECUDA;
-  if (cudaMemcpyAsync(b.sp, &sp, sizeof sp, cudaMemcpyHostToDevice, s) != cudaSuccess) return RTCUR_ECUDA;
-  if (cudaMemsetAsync(b.ticket, 0, sizeof(unsigned) * TK_COUNT, s) != cudaSuccess) return RTCUR_ECUDA;
+  k_noalloc_init<<<1, 32, 0, s>>>(b.st, b.sp, b.ticket, zeta, X, S);
+  if (cudaGetLastError() != cudaSuccess) return RTCUR_ECUDA;
   if (launch_table(g, b, 0, s) != cudaSuccess) return RTCUR_ECUDA;
   if (launch_dense(g, b, RTCUR_FORM_FP32, s) != cudaSuccess) return RTCUR_ECUDA;
   if (counts) {
