@@ -760,6 +760,11 @@ __device__ void cluster_barrier() {
 // this CTA's columns and rows, and a chunk of W columns for Y = W^T Q_r Sigma^-2.
 constexpr int kWChunk = 32;
 constexpr int kWarmMaxSteps = 12;  // subspace-iteration steps a warm attempt may take
+// Cold path: when the FP32 eigenvalues put lambda_r below kLowLambda lambda_1 (sigma_r / sigma_1
+// below 1e-2, where the FP32 eigenbasis stops resolving eigenvector r), kLowSteps FP64
+// subspace-iteration steps replace the Ogita-Aishima refinement.
+constexpr float kLowLambda = 1e-4f;
+constexpr int kLowSteps = 4;
 constexpr double kWarmGate = 1.5;  // attempt only if ||C||_F / lambda_r was below this last time
 
 // In-place Cholesky of the r x r SPD matrix G (row-major; the lower triangle is read and
@@ -899,9 +904,64 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
     sXc[t] = Xh[(long long)a * m + lo + j];
   }
   __syncthreads();
+  __shared__ int chol_ok;
+  // One FP64 subspace-iteration step with a Cholesky QR: X1 <- (M X1) L^-T, L L^T = (M X1)^T (M X1).
+  // False when the Cholesky fails, or when a pivot of L falls below min_pivot L_00 (a column of
+  // M X1 with no resolvable part outside the others); the same data in every CTA of the cluster
+  // gives a uniform outcome.
+  auto subspace_step = [&](double min_pivot) -> bool {
+    for (int t0 = tid >> 2; t0 < ((own * r + nq - 1) / nq) * nq; t0 += nq) {
+      const int t = t0;
+      const bool act = t < own * r;
+      int a = act ? t / r : 0, j = act ? t - a * r : 0;
+      double acc = 0.0;
+      if (act) {
+        const double* Ma = sM + (size_t)a * m;
+        for (int c = ql; c < m; c += 4) acc = fma(Ma[c], sX1[c * r + j], acc);
+      }
+      acc = quad_sum_d(acc);
+      if (act && ql == 0) Yw[(long long)(lo + a) * r + j] = acc;
+    }
+    cluster_barrier();
+    load_panel(sYw, Yw, m * r);
+    __syncthreads();
+    for (int t = wid; t < r * r; t += nw) {
+      int j = t / r, l = t % r;
+      double acc = 0.0;
+      for (int a = lane; a < m; a += 32) acc = fma(sYw[a * r + j], sYw[a * r + l], acc);
+      acc = warp_sum_d(acc);
+      if (lane == 0) Gq[t] = acc;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      chol_ok = chol_small(Gq, r, invd) ? 1 : 0;
+      for (int j = 1; j < r && chol_ok; ++j)
+        if (Gq[j * r + j] <= min_pivot * Gq[0]) chol_ok = 0;
+    }
+    __syncthreads();
+    if (!chol_ok) return false;
+    for (int a = lo + tid; a < hi; a += blockDim.x) {
+      double y[RT_MAXR];
+#pragma unroll
+      for (int j = 0; j < RT_MAXR; ++j) {
+        if (j < r) {
+          double v = sYw[a * r + j];
+          for (int l = 0; l < j; ++l) v -= Gq[j * r + l] * y[l];
+          y[j] = v * invd[j];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < RT_MAXR; ++j)
+        if (j < r) X1[(long long)a * r + j] = y[j];
+    }
+    cluster_barrier();
+    load_panel(sX1, X1, m * r);
+    __syncthreads();
+    return true;
+  };
+  int oa_steps = g.refine_steps;  // Ogita-Aishima steps of the cold path
   if (mode == 0) {
-    // warm start: the previous iteration's top-r basis, then FP64 subspace iteration with a
-    // Cholesky QR per step: X <- (M X) L^-T, L L^T = (M X)^T (M X)
+    // warm start: the previous iteration's top-r basis, then FP64 subspace iteration
     for (int t = tid; t < own * r; t += blockDim.x) {
       int a = lo + t / r, j = t % r;
       X1[(long long)a * r + j] = Qr[(long long)a * r + j];
@@ -909,54 +969,11 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
     cluster_barrier();
     load_panel(sX1, X1, m * r);
     __syncthreads();
-    __shared__ int chol_ok;
   warm_steps:
-    for (int it = 0; it < wsteps; ++it) {
-      for (int t0 = tid >> 2; t0 < ((own * r + nq - 1) / nq) * nq; t0 += nq) {
-        const int t = t0;
-        const bool act = t < own * r;
-        int a = act ? t / r : 0, j = act ? t - a * r : 0;
-        double acc = 0.0;
-        if (act) {
-          const double* Ma = sM + (size_t)a * m;
-          for (int c = ql; c < m; c += 4) acc = fma(Ma[c], sX1[c * r + j], acc);
-        }
-        acc = quad_sum_d(acc);
-        if (act && ql == 0) Yw[(long long)(lo + a) * r + j] = acc;
-      }
-      cluster_barrier();
-      load_panel(sYw, Yw, m * r);
-      __syncthreads();
-      for (int t = wid; t < r * r; t += nw) {
-        int j = t / r, l = t % r;
-        double acc = 0.0;
-        for (int a = lane; a < m; a += 32) acc = fma(sYw[a * r + j], sYw[a * r + l], acc);
-        acc = warp_sum_d(acc);
-        if (lane == 0) Gq[t] = acc;
-      }
-      __syncthreads();
-      if (tid == 0) chol_ok = chol_small(Gq, r, invd) ? 1 : 0;
-      __syncthreads();
-      if (!chol_ok) return;  // uniform across the cluster (same data): the full path runs
-      for (int a = lo + tid; a < hi; a += blockDim.x) {
-        double y[RT_MAXR];
-#pragma unroll
-        for (int j = 0; j < RT_MAXR; ++j) {
-          if (j < r) {
-            double v = sYw[a * r + j];
-            for (int l = 0; l < j; ++l) v -= Gq[j * r + l] * y[l];
-            y[j] = v * invd[j];
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < RT_MAXR; ++j)
-          if (j < r) X1[(long long)a * r + j] = y[j];
-      }
-      cluster_barrier();
-      load_panel(sX1, X1, m * r);
-      __syncthreads();
-    }
+    for (int it = 0; it < wsteps; ++it)
+      if (!subspace_step(0.0)) return;  // not certified: the full path runs
     wtotal += wsteps;
+    oa_steps = 0;
   } else {
   for (int t = tid; t < own * r; t += blockDim.x) {
     int a = lo + t / r, j = t % r;
@@ -965,9 +982,24 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
   cluster_barrier();
   load_panel(sX1, X1, m * r);
   __syncthreads();
+  // lambda_r below the resolution of the FP32 eigenbasis (its eigenvalues carry an absolute
+  // error of about m 2^-24 lambda_1): the FP32 basis does not resolve eigenvector r from the
+  // complement, and the refinement below, which divides by FP32 eigenvalue gaps, cannot repair
+  // it. FP64 subspace iteration from that basis can: each step shrinks the complement's share by
+  // lambda_{r+1} / lambda_r. When eigenvalue r itself is at FP64's noise level (a rank-deficient
+  // W, whose direction r the SVD_r cutoff drops anyway) a step finds no resolvable column and the
+  // refinement runs as before, from the last good basis.
+  if (lam[top[r - 1]] < kLowLambda * lam[top[0]]) {
+    int done = 0;
+    for (int it = 0; it < kLowSteps; ++it) {
+      if (!subspace_step(1e-12)) break;
+      ++done;
+    }
+    if (done == kLowSteps) oa_steps = 0;
+  }
   }
   PHASE_MARK(tph, "ref.init");
-  for (int step = 0; step < ((mode == 0) ? 0 : g.refine_steps); ++step) {
+  for (int step = 0; step < oa_steps; ++step) {
     // S1: Yw = M X1 on own rows (one quad per output)
     for (int t0 = tid >> 2; t0 < ((own * r + nq - 1) / nq) * nq; t0 += nq) {
       const int t = t0;
