@@ -30,14 +30,17 @@ sys.path.insert(0, ROOT)
 METRIC = "RTCUR iters/s & time-to-1e-5 at 800³ rank 5: BF16/TF32 vs FP32 plain, % HBM roofline"
 
 
-# DRAM bytes (read + write) per launch of the FP32 fused dense pass, from one ncu capture of the
-# 400^3 pass (dram__bytes_read.sum 259.3 MB + dram__bytes_write.sum 194.9 MB) scaled by the
-# element count to 800^3. The write counter undercounts: up to the L2 size of S is still dirty in
-# L2 when the captured launch ends. Must be dropped whenever the kernel changes.
-DENSE_TRAFFIC = {(800, 800, 800): (259.335680e6 + 195.482624e6) * 8.0,
-                 (400, 400, 400): 259.335680e6 + 195.482624e6}
-DENSE_TRAFFIC_SOURCE = ("ncu --set full of k_dense_tma<5,0> at 400^3 (one launch), "
-                        "scaled by elements to the timed size")
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e nominal bandwidth (context for the roofline fraction)
+
+# DRAM bytes (read + write) of one launch of the FP32 fused dense pass k_dense_tma<5,0>, from an
+# ncu capture of two back-to-back launches at 600^3 without cache control (the second launch: the
+# dirty lines the first left in L2 are written back inside it, as its own are after it), scaled
+# by the element count. None until that capture exists; must be dropped whenever the kernel
+# changes.
+DENSE_TRAFFIC_PER_ELEMENT = 1734182400.0 / 216e6  # 8.029 B per element
+DENSE_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_dense_tma<5,0>, 600^3, "
+                        "second of two back-to-back launches, --cache-control none, scaled by elements "
+                        "(profiles/k_dense_tma_traffic_600.md)")
 
 
 def parse():
@@ -65,6 +68,15 @@ def workload_name(a):
     return (f"RTCUR-{a.variant} {a.scope.upper()} scope, {a.size}^3 FP32 Gaussian Tucker rank "
             f"({a.rank},{a.rank},{a.rank}), {int(a.alpha * 100)}% outliers U[-10 mean|L*|, 10 mean|L*|], "
             f"v={a.upsilon:g}, gamma=0.7, zeta0=max|X|, tol 1e-5")
+
+
+def workload_config(a, p, world=1):
+    """The workload's description, identical in both arms' JSON lines."""
+    return {"workload": workload_name(a), "dims": list(p.dims), "ranks": list(p.ranks), "nI": p.m,
+            "nJ": p.q, "variant": a.variant, "scope": a.scope,
+            "l2": (f"inputs larger than L2 (X is {p.X.nbytes / 1e9:.2f} GB, L2 0.13 GB), no flush"
+                   if p.X.nbytes > 2 * 129e6 else "inputs smaller than L2 (a small case, not a bench figure)"),
+            "parallelism": "replicas" if world > 1 else "single GPU"}
 
 
 def make_problem(a):
@@ -134,40 +146,92 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def oracle_iteration_time(p, sets, a, budget_s=20.0):
-    """The FP64 oracle as it stands, timed on the host cores on a bounded sample of one
-    iteration: the full sampled step (gather, HT, Fiber CUR with LAPACK SVD, e^(k)) plus, in
-    the FULL scope, the dense threshold pass over a slab of mode-1 rows scaled to the tensor."""
+class OracleFull:
+    """Algorithm 1 in the FULL scope, one iteration per ``step()``, run by the FP64 oracle as it
+    stands: the decay, Step (I) over the whole tensor (L^(k) formed in full by the literal chain,
+    HT, the residual), then the sampled step (gather, Fiber CUR with LAPACK SVD, e^(k+1))."""
+
+    def __init__(self, p, sets, variant):
+        from oracle import rtcur_oracle as O
+        self.O = O
+        self.p, self.sets, self.variant = p, sets, variant
+        self.Xd = p.X.astype(np.float64)  # set-up (the oracle works in FP64)
+        self.st = O.RTCURState()
+        self.zeta = p.zeta0
+        self.k = 0
+
+    def step(self):
+        O, p = self.O, self.p
+        self.zeta *= p.gamma
+        s = self.sets[0] if self.variant == "F" else self.sets[self.k % len(self.sets)]
+        D = self.Xd - self.st.full(p.dims)
+        S = O.hard_threshold(D, self.zeta)
+        resid = float(np.sum((D - S) ** 2))
+        del D, S
+        self.st, info = O.rtcur_step(self.Xd, self.st, s, self.zeta, p.ranks)
+        self.k += 1
+        return resid, info["e"]
+
+
+def oracle_full_iterations(p, sets, variant, n_untimed, n_timed):
+    """Wall time of ``n_timed`` whole FULL-scope oracle iterations after ``n_untimed`` (the first
+    iteration, with L^(0) = 0, is cheaper than the rest)."""
+    orc = OracleFull(p, sets, variant)
+    for _ in range(n_untimed):
+        orc.step()
+    times = []
+    for _ in range(n_timed):
+        t0 = time.perf_counter()
+        orc.step()
+        times.append(time.perf_counter() - t0)
+    return times
+
+
+def oracle_sampled_solve(p, sets, variant):
+    """The oracle's whole SAMPLED-scope solve to tol (Sec. 3.3's partial S update: the paper's
+    efficient form), timed; returns (seconds, result)."""
     from oracle import rtcur_oracle as O
-    X = p.X
-    Xd = X.astype(np.float64)  # setup, untimed (the oracle works in FP64)
-    st = O.RTCURState()
-    zeta = p.zeta0
-    ts = []
-    t_begin = time.perf_counter()
-    k = 0
-    while True:
-        zeta *= p.gamma
-        s = sets[0] if a.variant == "F" else sets[k % len(sets)]
-        t0 = time.perf_counter()
-        st, info = O.rtcur_step(Xd, st, s, zeta, p.ranks)
-        ts.append(time.perf_counter() - t0)
-        k += 1
-        if k >= 3 or time.perf_counter() - t_begin > budget_s * 0.6:
-            break
-    t_step = float(np.median(ts))
-    t_dense, rows_done = 0.0, 0
-    if a.scope == "full":
-        d0 = p.dims[0]
-        rows = max(1, min(d0, int(d0 * 0.05)))
-        t0 = time.perf_counter()
-        Lslab = O.tucker_full(st.core, [st.factors[0][:rows]] + list(st.factors[1:]))
-        Sslab = O.hard_threshold(X[:rows].astype(np.float64) - Lslab, zeta)
-        _ = float(np.sum((X[:rows] - Lslab - Sslab) ** 2))
-        t_dense = (time.perf_counter() - t0) * d0 / rows
-        rows_done = rows
-    return t_step + t_dense, {"t_sampled_step_s": t_step, "t_dense_pass_s": t_dense,
-                              "steps_timed": len(ts), "dense_rows_timed": rows_done}
+    t0 = time.perf_counter()
+    ref = O.rtcur(p.X, p.ranks, sets, p.zeta0, p.gamma, p.tol, p.max_iter, variant)
+    return time.perf_counter() - t0, ref
+
+
+def oracle_parity(p, sets, variant, gpu, ref, form_s=None):
+    """The GPU solve's results (host copies at the comparison entries, ``gather_for_oracle``)
+    against the oracle's solve ``ref``: iterations, histories, L, and the support of S split into
+    in-band / L-explained / unexplained differences. ``form_s`` maps other dense forms to their S
+    at the same entries (same iterates, only the dense pass differs)."""
+    from oracle import compare as CMP
+    k = ref["iters"]
+    out = {"iters_gpu": gpu["iters"], "iters_oracle": k, "iters_equal": gpu["iters"] == k}
+    if gpu["iters"] != k or k == 0:
+        return out
+    last = sets[0] if variant == "F" else sets[k - 1]
+    groups = CMP.entry_groups(p.dims)
+    assert all(all(np.array_equal(a, b) for a, b in zip(G, H)) for G, H in zip(groups, gpu["groups"]))
+    orc = CMP.oracle_values(ref, p.dims, last, groups)
+    z = np.asarray(ref["hist"]["zeta"])
+    e = np.asarray(ref["hist"]["e"])
+    out["zeta_max_rel_diff"] = float(np.max(np.abs(gpu["zeta_hist"] - z) / z))
+    out["e_max_abs_diff"] = float(np.max(np.abs(gpu["e_hist"] - e)))
+    out["e_max_rel_diff"] = float(np.max(np.abs(gpu["e_hist"] - e) / np.maximum(e, 1e-300)))
+    rel, fl = CMP.compare_entries(p.X, groups, orc, gpu["L_sample"], gpu["L_groups"], gpu["S_groups"],
+                                  gpu["Lprev_groups"], ref["zeta"])
+    out["rel_L"] = rel
+    out["support"] = fl
+    out["entries"] = ("L: every sampled entry of the last iteration + a seeded 100^3 grid + 4 "
+                      "mode-1 slabs; S: the grid and the slabs")
+    if form_s:
+        # a reduced-precision dense pass evaluates L^(k-1) itself: its flips are L-explained within
+        # the form's evaluation error (relative to max|L|), the same bands as the GPU form tests
+        band = {"fp32_plain": 2e-6, "bf16": 1e-4, "tf32": 4e-3, "fp32_compressed_S": 0.0}
+        maxL = max(float(np.max(np.abs(v))) for v in orc["Lprev_groups"])
+        out["forms"] = {}
+        for name, Sg in form_s.items():
+            _, f2 = CMP.compare_entries(p.X, groups, orc, gpu["L_sample"], gpu["L_groups"], Sg,
+                                        gpu["Lprev_groups"], ref["zeta"], extra=band[name] * maxL)
+            out["forms"][name] = dict(f2, evaluation_band=f"{band[name]:g} max|L|")
+    return out
 
 
 def cpu_cores():
@@ -178,24 +242,24 @@ def cpu_cores():
 
 
 def run_reference(a, rank, world):
+    """The reference arm: the FP64 oracle as it stands on the host cores, one whole FULL-scope
+    iteration of the same workload per step (W untimed, then K timed; nothing extrapolated)."""
     if rank != 0:
         return
     p, sets = make_problem(a)
     K, W = a.steps, a.warmup
-    times = []
-    for _ in range(max(1, min(K, 3))):
-        t, det = oracle_iteration_time(p, sets, a)
-        times.append(t)
-    t = float(np.median(times))
-    value = 1.0 / t
+    times = oracle_full_iterations(p, sets, a.variant, W, K)
+    t = float(np.sum(times))
+    value = K / t
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
-        "steps": K, "warmup": W, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "steps": K, "warmup": W, "ms_per_step": t / K * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(a)},
+        "config": workload_config(a, p, world),
         "cpu_baseline": {"value": value, "unit": "iters/s", "cores": cpu_cores(), "kind": "oracle",
-                         "sample": "median of bounded samples: one oracle iteration's sampled step "
-                                   "plus a 5% slab of the dense pass scaled to the tensor"},
+                         "sample": f"{K} whole FULL-scope oracle iterations ({W + 1}..{W + K}) of the "
+                                   f"workload after {W} untimed ones, each timed; numpy elementwise "
+                                   "steps run on one core, LAPACK/BLAS on all"},
         "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -248,8 +312,13 @@ def run_batched(dev):
         for pl in plans:
             rt.rtcur_destroy(pl)
     same = all(x.iters == y.iters and x.e == y.e for x, y in zip(seq, bat))
+    # the tuner times the refinement cluster size at the workload's own v = 3 (and v = 4): it may
+    # not lower v for speed, and every candidate must recover as many planted L* as the best
+    Ls = [torch.from_numpy(p.L_star.astype(np.float32)).to(dev) for p in probs]
     tuned = autotune.tune_batch(X, [p.dims for p in probs], [p.ranks for p in probs],
-                                [p.zeta0 for p in probs], variant="R", tol=1e-5, max_iter=100)
+                                [p.zeta0 for p in probs], variant="R", tol=1e-5, max_iter=100,
+                                upsilons=(3.0, 4.0), min_upsilon=3.0, L_star=Ls)
+    del Ls
     return {
         "workload": "64 uneven 3-mode FP32 problems, dims U{64..320}, ranks U{2..10}, outliers "
                     "U[10%, 40%], RTCUR-R, v=3, tol 1e-5 (seeds 0..63)",
@@ -260,7 +329,9 @@ def run_batched(dev):
         "all_converged": all(r.status == rt.OK for r in bat),
         "batched_equals_sequential": same,
         "tuned": {"cluster": tuned["cluster"], "upsilon": tuned["upsilon"],
-                  "graph_ms": tuned["ms"], "table": tuned["table"]},
+                  "graph_ms": tuned["ms"], "table": tuned["table"],
+                  "rule": "fastest of the candidates at v >= 3 that converge on every problem and "
+                          "recover (||L - L*||/||L*|| <= 1e-3) as many problems as the best"},
         "timing": "wall clock around the public calls (index upload, graph launch, results)",
     }
 
@@ -309,6 +380,84 @@ def run_adjoint(dev):
                         "seed dL + rtcur_backward (FP64 pinv adjoints)"}
 
 
+def take(T, coords):
+    """Host FP64 copy of a device tensor's entries at integer coordinate arrays."""
+    import torch
+    idx = tuple(torch.from_numpy(np.ascontiguousarray(np.asarray(c).reshape(-1))).to(T.device) for c in coords)
+    return T[idx].cpu().numpy().astype(np.float64).reshape(np.asarray(coords[0]).shape)
+
+
+def comparison_coords(p, sets, variant, iters):
+    """Coordinates the oracle comparison reads: the last iteration's sampled entries (R, then the
+    fibers) and the entry groups (a seeded 100^3 grid and 4 mode-1 slabs). Built without the
+    oracle: the same recipe as the comparison's own groups (checked there by shape)."""
+    rng = np.random.default_rng(1234)
+    dims = p.dims
+    groups = [[np.sort(rng.choice(int(d), size=min(int(d), 100), replace=False)) for d in dims]]
+    for s0 in np.sort(rng.choice(int(dims[0]), size=min(int(dims[0]), 4), replace=False)):
+        groups.append([np.array([s0])] + [np.arange(int(d)) for d in dims[1:]])
+    last = sets[0] if variant == "F" else sets[max(iters - 1, 0) % len(sets)]
+    samp = [np.meshgrid(*last["I"], indexing="ij")]
+    for i in range(len(dims)):
+        rest = int(np.prod([d for j, d in enumerate(dims) if j != i]))
+        J = np.asarray(last["J"][i])
+        rem = J.copy()
+        oc = [None] * len(dims)
+        for l in reversed(range(len(dims))):
+            if l == i:
+                continue
+            oc[l] = rem % dims[l]
+            rem = rem // dims[l]
+        assert rest > 0
+        samp.append([np.broadcast_to(np.arange(dims[i])[:, None], (dims[i], J.size)) if l == i else
+                     np.broadcast_to(oc[l][None, :], (dims[i], J.size)) for l in range(len(dims))])
+    return groups, samp
+
+
+def gather_for_oracle(p, sets, variant, res, L, S, Lprev):
+    """Host copies of a GPU solve's results at the comparison entries."""
+    groups, samp = comparison_coords(p, sets, variant, res.iters)
+    grids = [np.meshgrid(*G, indexing="ij") for G in groups]
+    return {"groups": groups, "iters": res.iters, "e_hist": np.asarray(res.e_hist),
+            "zeta_hist": np.asarray(res.zeta_hist),
+            "L_sample": np.concatenate([take(L, c).ravel() for c in samp]),
+            "L_groups": [take(L, c) for c in grids], "S_groups": [take(S, c) for c in grids],
+            "Lprev_groups": [take(Lprev, c) for c in grids]}
+
+
+def solve_timed(rt, plan, X, idx, L, S, sh, stream, max_iter, reps=7, skip=2):
+    """Whole solves from X resident (index upload, max|X|, the graph-driven loop, L and S output):
+    CUDA-event times of ``reps`` solves, the first ``skip`` untimed; returns (median ms, all, last res)."""
+    import torch
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ts, res = [], None
+    for rep in range(reps):
+        ev0.record(stream)
+        res = rt.rtcur_solve(plan, X.data_ptr(), idx, L.data_ptr() if L is not None else 0,
+                             S.data_ptr() if S is not None else 0, sh, max_iter=max_iter)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if rep >= skip:
+            ts.append(ev0.elapsed_time(ev1))
+    return float(np.median(ts)), ts, res
+
+
+def iterations_timed(rt, plan, X, idx, S, sh, stream, K, W):
+    """W untimed then K timed iterations (rtcur_iterate), CUDA events on the launching stream."""
+    import torch
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    rt.rtcur_begin(plan, X.data_ptr(), idx, S.data_ptr() if S is not None else 0, sh)
+    rt.rtcur_iterate(plan, W, sh)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    rt.rtcur_iterate(plan, K, sh)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1)
+
+
 def run_ours(a, rank, world):
     import torch
     from paper_2108_10448_gb300 import rtcur as rt
@@ -351,7 +500,8 @@ def run_ours(a, rank, world):
         ev1.record(stream)
         torch.cuda.synchronize()
     ms, value = aggregate_replicas(ev0.elapsed_time(ev1), K, world, dev)
-    res_it = rt.rtcur_finish(plan, 0, 0, sh, max_iter=max_iter)
+    rt.rtcur_finish(plan, 0, 0, sh, max_iter=max_iter)
+    N = int(np.prod(p.dims))
     # --- dominant kernel alone: the dense fused pass, same launch configuration ---
     roof = None
     if scope == rt.SCOPE_FULL:
@@ -363,24 +513,41 @@ def run_ours(a, rank, world):
         ev1.record(stream)
         torch.cuda.synchronize()
         dms = ev0.elapsed_time(ev1) / nl
-        N = int(np.prod(p.dims))
         alg_bytes = 8.0 * N  # 4 B read of X + 4 B write of S per element
         peak, src = peaks()
         achieved = alg_bytes / (dms / 1e3) / 1e9
+        traffic = (DENSE_TRAFFIC_PER_ELEMENT * N
+                   if DENSE_TRAFFIC_PER_ELEMENT is not None and p.ranks[-1] == 5 else None)
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": DENSE_TRAFFIC.get(tuple(p.dims)) if p.ranks[-1] == 5 else None,
-                "traffic_source": DENSE_TRAFFIC_SOURCE if tuple(p.dims) in DENSE_TRAFFIC else None,
-                "kernel": f"k_dense_tma<{p.ranks[-1]},0>",
-                "ms_per_launch": dms, "peak_source": f"{src} (burst copy bandwidth)",
+                "frac": achieved / peak, "traffic": traffic,
+                "traffic_source": DENSE_TRAFFIC_SOURCE if traffic is not None else None,
+                "kernel": f"k_dense_tma<{p.ranks[-1]},0>", "ms_per_launch": dms,
+                "peak_source": f"{src} (burst copy bandwidth); the >= 0.70 target is judged on it",
+                "frac_of_nominal": achieved / NOMINAL_HBM_GBS, "nominal_peak": NOMINAL_HBM_GBS,
+                "iteration_frac": alg_bytes / (ms / K / 1e3) / 1e9 / peak,
                 "algorithmic_bytes_per_launch": alg_bytes}
+    # --- time to tolerance: whole solve from X resident, one graph launch; median of 5 after 2 ---
+    ttt_ms, ttts, res = solve_timed(rt, plan, X, idx, L, S, sh, stream, max_iter)
+    parity_gpu = {}
+    want_parity = rank == 0 and not a.no_cpu_baseline and res.iters >= 1
+    if want_parity:
+        Lprev = torch.empty_like(X)
+        pp = rt.rtcur_create(p.dims, p.ranks, p.m, p.q, p.zeta0, p.gamma, p.tol, max(res.iters - 1, 1),
+                             variant, rt.make_options(scope=scope))
+        if res.iters > 1:
+            rt.rtcur_solve(pp, X.data_ptr(), idx, Lprev.data_ptr(), 0, sh, max_iter=res.iters - 1)
+        else:
+            Lprev.zero_()
+        rt.rtcur_destroy(pp)
+        torch.cuda.synchronize()
+        parity_gpu[a.variant] = gather_for_oracle(p, sets, a.variant, res, L, S, Lprev)
+        del Lprev
     # --- dense-pass forms: same iterates, different evaluation of L in the dense pass ---
-    forms_out = None
+    forms_out, form_S = None, {}
     if scope == rt.SCOPE_FULL and not a.no_forms:
         forms_out = {}
-        S_ref = S.clone()
-        rt.rtcur_threshold_dense(plan, 1, sh)  # FP32 form at the plan's current state
-        torch.cuda.synchronize()
-        S_ref.copy_(S)
+        groups, _ = comparison_coords(p, sets, a.variant, res.iters)
+        grids = [np.meshgrid(*G, indexing="ij") for G in groups]
         for name, form, sfmt in (("fp32_plain", rt.FORM_FP32_PLAIN, rt.S_DENSE), ("bf16", rt.FORM_BF16, rt.S_DENSE),
                                  ("tf32", rt.FORM_TF32, rt.S_DENSE),
                                  ("fp32_compressed_S", rt.FORM_FP32, rt.S_COMPRESSED)):
@@ -391,14 +558,7 @@ def run_ours(a, rank, world):
                 forms_out[name] = {"unavailable": str(exc)}
                 continue
             Sf = torch.empty_like(X)
-            rt.rtcur_begin(fp, X.data_ptr(), idx, Sf.data_ptr(), sh)
-            rt.rtcur_iterate(fp, W, sh)
-            torch.cuda.synchronize()
-            ev0.record(stream)
-            rt.rtcur_iterate(fp, K, sh)
-            ev1.record(stream)
-            torch.cuda.synchronize()
-            fms = ev0.elapsed_time(ev1)
+            fms = iterations_timed(rt, fp, X, idx, Sf, sh, stream, K, W)
             rt.rtcur_threshold_dense(fp, 2, sh)
             torch.cuda.synchronize()
             ev0.record(stream)
@@ -406,37 +566,71 @@ def run_ours(a, rank, world):
             ev1.record(stream)
             torch.cuda.synchronize()
             dms_f = ev0.elapsed_time(ev1) / 5
-            N = float(np.prod(p.dims))
             fbytes, extra = 8.0 * N, {}
             if sfmt == rt.S_COMPRESSED:
                 c = rt.rtcur_get_s_compressed(fp, sh)
                 # read X, write the nonzero values and the mask words
                 fbytes = 4.0 * N + 4.0 * c["nnz"] + 4.0 * c["rows"] * c["words_per_row"]
-                rt.rtcur_decode_s(fp, Sf.data_ptr(), sh)
-                torch.cuda.synchronize()
-                extra = {"nnz": c["nnz"], "bytes_per_element": fbytes / N,
-                         "S_bit_equal_to_fp32": bool(torch.equal(Sf, S_ref))}
-            mism = int(((Sf != 0) != (S_ref != 0)).sum().item())
+                extra = {"nnz": c["nnz"], "bytes_per_element": fbytes / N}
+            # whole solve to tolerance with this form: S^(k) of the final iterate
+            f_ttt, _, fres = solve_timed(rt, fp, X, idx, None, Sf, sh, stream, max_iter, reps=3, skip=1)
+            if sfmt == rt.S_COMPRESSED:
+                extra["S_bit_equal_to_fp32"] = bool(torch.equal(Sf, S))
+            mism = int(((Sf != 0) != (S != 0)).sum().item())
+            if want_parity and fres.iters == res.iters:
+                form_S[name] = [take(Sf, c) for c in grids]
             rt.rtcur_destroy(fp)
+            del Sf
             forms_out[name] = {"iters_per_s": K / (fms / 1e3), "ms_per_iter": fms / K,
-                               "dense_ms": dms_f,
-                               "dense_gbs": fbytes / (dms_f / 1e3) / 1e9,
-                               "S_support_mismatch_vs_fp32": mism,
-                               "note": "same CUR iterates as the FP32 form; only S differs, near the threshold"
-                                       if sfmt == rt.S_DENSE else
-                                       "the FP32 form with S written as support bitmask + nonzero values", **extra}
+                               "dense_ms": dms_f, "dense_gbs": fbytes / (dms_f / 1e3) / 1e9,
+                               "time_to_tol_ms": f_ttt, "iters": fres.iters,
+                               "S_support_mismatch_vs_fp32_final": mism, **extra}
         forms_out["fp32_fused"] = {"iters_per_s": value / world, "ms_per_iter": ms / K,
-                                   "dense_ms": roof["ms_per_launch"] if roof else None}
-    # --- time to tolerance: whole solve from X resident, one graph launch; median of 5 after 2 ---
-    ttts = []
-    for rep in range(7):
-        ev0.record(stream)
-        res = rt.rtcur_solve(plan, X.data_ptr(), idx, L.data_ptr(), S.data_ptr(), sh, max_iter=max_iter)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        if rep >= 2:
-            ttts.append(ev0.elapsed_time(ev1))
-    ttt_ms = float(np.median(ttts))
+                                   "dense_ms": roof["ms_per_launch"] if roof else None,
+                                   "time_to_tol_ms": ttt_ms, "iters": res.iters}
+        forms_out["note"] = ("every form runs the same CUR iterates (the sampled chain is FP32/FP64 in "
+                             "all of them); only the dense pass's evaluation of L, hence S near the "
+                             "threshold, differs. S support against the oracle: support_vs_oracle.forms")
+    # --- the other variant at the same workload (RTCUR-R when the main line is F, and back) ---
+    other = "R" if a.variant == "F" else "F"
+    var_out = None
+    if world == 1:
+        o_sets = synth.draw_index_sets(p.dims, p.m, p.q, seed=a.seed, n_sets=100 if other == "R" else 1)
+        o_idx = synth.pack_index_sets(o_sets)
+        ov = rt.VARIANT_R if other == "R" else rt.VARIANT_F
+        op = rt.rtcur_create(p.dims, p.ranks, p.m, p.q, p.zeta0, p.gamma, p.tol, max_iter, ov,
+                             rt.make_options(scope=scope))
+        oms = iterations_timed(rt, op, X, o_idx, S, sh, stream, K, W)
+        o_ttt, o_ts, ores = solve_timed(rt, op, X, o_idx, L, S, sh, stream, max_iter)
+        rt.rtcur_destroy(op)
+        var_out = {"variant": other, "iters_per_s": K / (oms / 1e3), "ms_per_iter": oms / K,
+                   "time_to_tol": {"ms": o_ttt, "runs_ms": o_ts, "iters": ores.iters, "e": ores.e,
+                                   "status": ores.status}}
+        if want_parity and ores.iters >= 1:
+            Lprev = torch.empty_like(X)
+            pp = rt.rtcur_create(p.dims, p.ranks, p.m, p.q, p.zeta0, p.gamma, p.tol,
+                                 max(ores.iters - 1, 1), ov, rt.make_options(scope=scope))
+            if ores.iters > 1:
+                rt.rtcur_solve(pp, X.data_ptr(), o_idx, Lprev.data_ptr(), 0, sh, max_iter=ores.iters - 1)
+            else:
+                Lprev.zero_()
+            rt.rtcur_destroy(pp)
+            torch.cuda.synchronize()
+            parity_gpu[other] = gather_for_oracle(p, o_sets, other, ores, L, S, Lprev)
+            del Lprev
+    # --- SAMPLED scope (the paper's efficient form, Sec. 3.3): time to 1e-5, both variants ---
+    sampled_ttt = {}
+    if world == 1:
+        for v in ("F", "R"):
+            v_sets = sets if v == a.variant else synth.draw_index_sets(
+                p.dims, p.m, p.q, seed=a.seed, n_sets=100 if v == "R" else 1)
+            sp_ = rt.rtcur_create(p.dims, p.ranks, p.m, p.q, p.zeta0, p.gamma, p.tol, max_iter,
+                                  rt.VARIANT_R if v == "R" else rt.VARIANT_F,
+                                  rt.make_options(scope=rt.SCOPE_SAMPLED))
+            v_ms, v_ts, vres = solve_timed(rt, sp_, X, synth.pack_index_sets(v_sets), L, None, sh, stream, max_iter)
+            rt.rtcur_destroy(sp_)
+            sampled_ttt[v] = {"ms": v_ms, "runs_ms": v_ts, "iters": vres.iters, "e": vres.e,
+                              "status": vres.status}
     # --- end to end through the C ABI from pinned host buffers ---
     Xh = torch.from_numpy(p.X).pin_memory()
     Lh = torch.empty_like(Xh).pin_memory()
@@ -450,6 +644,7 @@ def run_ours(a, rank, world):
     e2e_s = time.perf_counter() - t0
     e2e_val = world * res_e2e.iters / e2e_s
     rt.rtcur_destroy(plan)
+    del Xd, Xh, Lh
     if rank != 0:
         return
     n_modes = 3
@@ -458,11 +653,8 @@ def run_ours(a, rank, world):
         "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": K,
         "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_name(a), "dims": list(p.dims), "ranks": list(p.ranks),
-                   "nI": p.m, "nJ": p.q, "variant": a.variant, "scope": a.scope,
-                   "dense_form": "fp32 fused (FMA last-mode product)", "pinv": "fp64",
-                   "l2": f"inputs larger than L2 (X is {p.X.nbytes / 1e9:.2f} GB, L2 0.13 GB), no flush",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "config": workload_config(a, p, world),
+        "implementation": {"dense_form": "fp32 fused (FMA last-mode product)", "pinv": "fp64"},
         "time_to_tol": {"ms": ttt_ms, "runs_ms": ttts, "iters": res.iters, "e": res.e, "status": res.status,
                         "warm_hits": res.warm_hits, "statistic": "median of 5 solves after 2 warm-up solves",
                         "includes": "index upload, max|X|, the graph-driven loop, L and S output"},
@@ -470,19 +662,45 @@ def run_ours(a, rank, world):
                 "h2d_bytes_per_step": int(p.X.nbytes), "d2h_bytes_per_step": int(p.X.nbytes),
                 "step": "one whole solve: H2D X, rtcur_solve to 1e-5, D2H L"},
         "roofline": roof,
+        "other_variant": var_out,
+        "sampled_time_to_tol": sampled_ttt or None,
         "forms": forms_out,
         "gpu_launches": launches_per_iter * K,
-        "batched": None if (a.no_batched or world > 1) else run_batched(dev),
-        "adjoint": None if (a.no_adjoint or world > 1) else run_adjoint(dev),
         "clocks": clk.summary(),
     }
+    del X, L, S
+    torch.cuda.empty_cache()
+    line["batched"] = None if (a.no_batched or world > 1) else run_batched(dev)
+    line["adjoint"] = None if (a.no_adjoint or world > 1) else run_adjoint(dev)
     if not a.no_cpu_baseline:
-        t_or, det = oracle_iteration_time(p, sets, a)
-        line["cpu_baseline"] = {"value": 1.0 / t_or, "unit": "iters/s", "cores": cpu_cores(),
-                                "kind": "oracle",
-                                "sample": "one oracle iteration's sampled step (median of up to 3) "
-                                          "plus a 5% slab of the dense pass scaled to the tensor",
-                                **det}
+        # the oracle as it stands on the host cores: two whole FULL-scope iterations of the
+        # workload (after one untimed), then its SAMPLED-scope solves to tol, whose results are
+        # also compared with the GPU's
+        t_full = oracle_full_iterations(p, sets, a.variant, 1, 2)
+        line["cpu_baseline"] = {
+            "value": len(t_full) / float(np.sum(t_full)), "unit": "iters/s", "cores": cpu_cores(),
+            "kind": "oracle",
+            "sample": "2 whole FULL-scope iterations (2 and 3) of the workload by the FP64 oracle, "
+                      "each timed, nothing extrapolated; numpy elementwise steps on one core, "
+                      "LAPACK/BLAS on all",
+            "iteration_s": t_full}
+        orc_ttt, support = {}, {}
+        for v in ("F", "R"):
+            v_sets = sets if v == a.variant else synth.draw_index_sets(
+                p.dims, p.m, p.q, seed=a.seed, n_sets=100 if v == "R" else 1)
+            t_or, ref = oracle_sampled_solve(p, v_sets, v)
+            orc_ttt[v] = {"s": t_or, "iters": ref["iters"], "e": ref["e"],
+                          "gpu_sampled_ms": sampled_ttt.get(v, {}).get("ms"),
+                          "speedup": (t_or * 1e3 / sampled_ttt[v]["ms"]) if v in sampled_ttt else None}
+            if v in parity_gpu:
+                support[v] = oracle_parity(p, v_sets, v, parity_gpu[v], ref,
+                                           form_S if v == a.variant else None)
+            del ref
+        line["cpu_baseline"]["sampled_solve_to_tol"] = orc_ttt
+        line["cpu_baseline"]["sampled_note"] = ("the oracle's SAMPLED-scope solve to 1e-5 (the paper's "
+                                                "efficient method), beside the GPU's SAMPLED-scope "
+                                                "time to 1e-5 of the same problem and index sets")
+        line["support_vs_oracle"] = support
     print(json.dumps(line), flush=True)
 
 
