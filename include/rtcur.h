@@ -73,6 +73,15 @@ enum { RTCUR_FORM_FP32 = 0, RTCUR_FORM_FP32_PLAIN = 1, RTCUR_FORM_BF16 = 2, RTCU
  * 4 to 1.33 bytes per element). Needs dense_form FP32, d_n % 4 == 0, d_n <= 4096, r_n <= 8. */
 enum { RTCUR_S_DENSE = 0, RTCUR_S_COMPRESSED = 1 };
 
+/* Where the sampled step (Step (I) on the sample, Eq. partial S update, and the gathers of R and
+ * C_i) reads X from. FP32: the caller's tensor (default). BF16: a copy of X rounded to BF16
+ * (round to nearest even), made by rtcur_begin in plan memory (prod d_i x 2 bytes, allocated at
+ * create): the iterates are then those of the method applied to the BF16-rounded tensor (each
+ * sampled value carries up to 2^-9 relative rounding), while the FULL scope's dense pass and the
+ * outputs keep reading the FP32 X. FP32 values beyond BF16's range round to infinity and are
+ * reported as RTCUR_ENONFINITE. */
+enum { RTCUR_SAMPLE_X_FP32 = 0, RTCUR_SAMPLE_X_BF16 = 1 };
+
 /* Bits of rtcur_result.flags */
 enum {
   RTCUR_FLAG_RANK_DEFICIENT = 1, /* some SVD_{r_i} kept fewer than r_i singular values */
@@ -95,7 +104,8 @@ typedef struct rtcur_options {
                                 cluster): 0 = auto (16, else 8), or 2, 4, 8, 16; smaller clusters
                                 suit many concurrent problems (the batched form) */
   int32_t s_format;          /* RTCUR_S_*: format of S in the FULL scope; default DENSE */
-  int32_t reserved[4];       /* must be zero */
+  int32_t sample_x;          /* RTCUR_SAMPLE_X_*: what the sampled step reads X from; default FP32 */
+  int32_t reserved[3];       /* must be zero */
 } rtcur_options;
 
 /* Compressed S^(k) (s_format COMPRESSED), in device memory owned by the plan and overwritten by

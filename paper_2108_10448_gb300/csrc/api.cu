@@ -263,7 +263,7 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
   o.inband_rel = 1e-6;
   if (opt) {
     o = *opt;
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 3; ++i)
       if (o.reserved[i] != 0) return fail(nullptr, RTCUR_EINVAL, "options.reserved must be zero");
     if (o.refine_steps == 0 && o.jacobi_max_sweeps == 0 && o.inband_rel == 0.0) {
       o.refine_steps = 2; o.jacobi_max_sweeps = 30; o.inband_rel = 1e-6;
@@ -284,6 +284,10 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
     return fail(nullptr, RTCUR_EINVAL, "s_format must be DENSE (0) or COMPRESSED (1)");
   if (o.s_format == RTCUR_S_COMPRESSED && (o.scope != RTCUR_SCOPE_FULL || o.dense_form != RTCUR_FORM_FP32))
     return fail(nullptr, RTCUR_EINVAL, "s_format COMPRESSED needs the FULL scope and dense_form FP32");
+  if (o.sample_x != RTCUR_SAMPLE_X_FP32 && o.sample_x != RTCUR_SAMPLE_X_BF16)
+    return fail(nullptr, RTCUR_EINVAL, "sample_x must be FP32 (0) or BF16 (1)");
+  if (o.sample_x == RTCUR_SAMPLE_X_BF16 && o.checkpoint > 0)
+    return fail(nullptr, RTCUR_EINVAL, "sample_x BF16 cannot be combined with checkpoint (the adjoint is taken w.r.t. the FP32 X)");
 
   Geom g;
   memset(&g, 0, sizeof g);
@@ -350,6 +354,7 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
   g.sumMR = oQ;
   g.dense_form = o.dense_form;
   g.s_format = o.s_format;
+  g.sample_x = o.sample_x;
   {
     long long oDM = 0;
     for (int i = 0; i < n_modes; ++i) { g.offDM[i] = oDM; oDM += g.d[i] * g.m[i]; }
@@ -452,6 +457,7 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
   AL(b.tl_n, 1);
 #endif
   if (o.scope == RTCUR_SCOPE_FULL && g.s_format == RTCUR_S_DENSE) AL(p->S_internal, g.N);
+  if (g.sample_x == RTCUR_SAMPLE_X_BF16) AL(b.Xb, g.N);
   if (g.s_format == RTCUR_S_COMPRESSED) {
     const long long wpr = (g.d[n_modes - 1] + 31) / 32;
     AL(b.smask, g.rowsT * wpr);
@@ -521,6 +527,8 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
     e = prepare_jacobi(sm);
   }
   if (e == cudaSuccess) e = prepare_dense(g);
+  if (e == cudaSuccess) e = prepare_sample_kernels();
+  if (e == cudaSuccess) e = prepare_factor_kernels();
   if (e == cudaSuccess) {
     e = prepare_refine(p->g, o.refine_cluster);
     if (e == cudaErrorInvalidValue) {
@@ -580,6 +588,7 @@ rtcur_status rtcur_begin(rtcur_plan* p, const float* X, const int64_t* idx, floa
     CKC(p, cudaMemsetAsync(b.Rp[0], 0, sizeof(float) * g.nR, s));
   }
   CKC(p, launch_setup(g, b, p->zeta0, p->zeta0 <= 0.0 ? 1 : 0, s));
+  if (b.Xb) CKC(p, launch_x_bf16(g, b, X, s));  // the sampled step's BF16 copy of this X
   if (g.variant == RTCUR_VARIANT_F) CKC(p, launch_gather_x(g, b, s));
   p->X = X;
   p->S_work = S;

@@ -9,6 +9,8 @@
 //
 // Reductions are deterministic: per-block partials in a fixed slot, then the last block to
 // finish sums them in block order.
+#include <cuda_bf16.h>
+
 #include "../../include/rtcur.h"
 #include "rtcur_internal.cuh"
 
@@ -17,6 +19,13 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kHtBlocksFull = 2 * 152;
 constexpr int kMaxRedBlocks = 1024;
+
+// X at flat index `idx` as the sampled step reads it: the caller's FP32 tensor, or its BF16 copy
+// (sample_x BF16) widened back to FP32.
+__device__ __forceinline__ float sample_x_at(const Bufs& b, const float* X, long long idx) {
+  if (b.Xb) return __uint_as_float((unsigned)__ldg(b.Xb + idx) << 16);
+  return __ldg(X + idx);
+}
 
 __device__ __forceinline__ const long long* current_set(const Geom& g, const Bufs& b, int k) {
   long long s = (g.variant == 1) ? (long long)(k % g.n_sets) : 0;
@@ -107,8 +116,30 @@ __global__ void __launch_bounds__(kThreads) k_gather_x(Geom g, Bufs b) {
     sample_coords(g, set, e, p);
     long long row = table_row(g, p), col = p[g.n - 1];
     b.rc[e] = make_uint2((unsigned)row, (unsigned)col);
-    b.Xs[e] = __ldg(X + row * g.d[g.n - 1] + col);
+    b.Xs[e] = sample_x_at(b, X, row * g.d[g.n - 1] + col);
   }
+}
+
+// The BF16 copy of X for the sampled step (sample_x BF16): round to nearest even, four values per
+// thread from one float4 (the tensor is 16-byte aligned; a tail of N % 4 values is done singly).
+__device__ __forceinline__ unsigned short bf16_rne(float x) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+__global__ void __launch_bounds__(kThreads) k_x_bf16(long long N, const float* __restrict__ X,
+                                                     unsigned short* __restrict__ Xb) {
+  const long long n4 = N >> 2;
+  const long long stride = (long long)gridDim.x * kThreads;
+  for (long long v = (long long)blockIdx.x * kThreads + threadIdx.x; v < n4; v += stride) {
+    const float4 x = __ldcs(reinterpret_cast<const float4*>(X) + v);
+    ushort4 o;
+    o.x = bf16_rne(x.x);
+    o.y = bf16_rne(x.y);
+    o.z = bf16_rne(x.z);
+    o.w = bf16_rne(x.w);
+    reinterpret_cast<ushort4*>(Xb)[v] = o;
+  }
+  for (long long e = (n4 << 2) + (long long)blockIdx.x * kThreads + threadIdx.x; e < N; e += stride)
+    Xb[e] = bf16_rne(X[e]);
 }
 
 // Segment of entry e (0 = R, 1 + i = C_i).
@@ -149,7 +180,7 @@ __global__ void __launch_bounds__(kThreads) k_sample_ht(Geom g, Bufs b) {
       row = table_row(g, p);
       col = p[g.n - 1];
       b.rc[e] = make_uint2((unsigned)row, (unsigned)col);
-      x = __ldg(X + row * dn + col);
+      x = sample_x_at(b, X, row * dn + col);
     } else {
       uint2 rc = b.rc[e];
       row = rc.x;
@@ -313,8 +344,32 @@ cudaError_t launch_maxabs(const Geom& g, const Bufs& b, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// The sampled chain's kernels run beside the dense pass, whose persistent CTAs need the SM's
+// maximum shared-memory carveout. A block of another carveout on an SM keeps a dense CTA off it
+// until the block drains (the SM's L1/shared split changes only when it is idle), so the chain's
+// kernels ask for the same carveout.
+cudaError_t prepare_sample_kernels() {
+  const void* fns[] = {(const void*)k_setup, (const void*)k_maxabs, (const void*)k_gather_x,
+                       (const void*)k_x_bf16, (const void*)k_sample_ht, (const void*)k_sample_err,
+                       (const void*)k_commit};
+  for (const void* f : fns) {
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t launch_gather_x(const Geom& g, const Bufs& b, cudaStream_t s) {
   k_gather_x<<<grid_for(g.nS), kThreads, 0, s>>>(g, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_x_bf16(const Geom& g, const Bufs& b, const float* X, cudaStream_t s) {
+  long long blocks = (g.N / 4 + kThreads - 1) / kThreads;
+  if (blocks > 8 * 152) blocks = 8 * 152;  // grid-stride: a few waves of resident blocks
+  if (blocks < 1) blocks = 1;
+  k_x_bf16<<<(int)blocks, kThreads, 0, s>>>(g.N, X, b.Xb);
   return cudaGetLastError();
 }
 

@@ -44,6 +44,7 @@ struct Geom {
   int ck_iters;                  // iterations recorded for the adjoint (0: none)
   int s_format;                  // RTCUR_S_* of the FULL scope's S output
   int tile_rows;                 // rows per tile of the FP32 bulk-copy pass (compressed S layout)
+  int sample_x;                  // RTCUR_SAMPLE_X_*: the sampled step reads X (FP32) or its BF16 copy
   int nG;                       // prod r_i
   int rlast;                    // r_n
   long long d[RT_MAXN];
@@ -160,6 +161,8 @@ struct Bufs {
   // U_i^+ (sum q_i m_i doubles, q_i x m_i row-major)
   float* curF;
   double* curU;
+  // sample_x BF16: the BF16 copy of X the sampled step reads (N values, round to nearest even)
+  unsigned short* Xb;
 };
 
 // Workspace of the adjoint (rtcur_backward), 3-mode tensors. Per recorded iteration and mode:
@@ -221,6 +224,7 @@ enum { TK_SAMPLE = 0, TK_ERR = 1, TK_DENSE = 2, TK_MAXABS = 3, TK_DTILE = 4, TK_
 cudaError_t launch_setup(const Geom& g, const Bufs& b, double zeta0, int use_maxabs, cudaStream_t s);
 cudaError_t launch_maxabs(const Geom& g, const Bufs& b, cudaStream_t s);
 cudaError_t launch_gather_x(const Geom& g, const Bufs& b, cudaStream_t s);
+cudaError_t launch_x_bf16(const Geom& g, const Bufs& b, const float* X, cudaStream_t s);
 cudaError_t launch_sample_ht(const Geom& g, const Bufs& b, cudaStream_t s);
 cudaError_t launch_gram(const Geom& g, const Bufs& b, cudaStream_t s);
 cudaError_t launch_jacobi(const Geom& g, const Bufs& b, cudaStream_t s);
@@ -235,6 +239,8 @@ cudaError_t launch_commit(const Geom& g, const Bufs& b, unsigned long long handl
 cudaError_t launch_batch_any(State* const* sts, int count, unsigned long long handle, cudaStream_t s);
 cudaError_t launch_dense(const Geom& g, const Bufs& b, int form, cudaStream_t s);
 cudaError_t prepare_dense(const Geom& g);  // kernel attributes of the dense pass (call at create)
+cudaError_t prepare_sample_kernels();      // shared-memory carveout of the sampled chain's kernels
+cudaError_t prepare_factor_kernels();
 bool dense_form_supported(const Geom& g, int form);
 cudaError_t launch_plain_dense(const Geom& g, const Bufs& b, cudaStream_t s);
 cudaError_t launch_plain_prep(const Geom& g, const Bufs& b, cudaStream_t s);

@@ -18,13 +18,14 @@ SCOPE_SAMPLED, SCOPE_FULL = 0, 1
 FORM_FP32, FORM_FP32_PLAIN, FORM_BF16, FORM_TF32 = 0, 1, 2, 3
 FLAG_RANK_DEFICIENT, FLAG_TIE = 1, 2
 S_DENSE, S_COMPRESSED = 0, 1
+SAMPLE_X_FP32, SAMPLE_X_BF16 = 0, 1
 
 
 class rtcur_options(C.Structure):
     _fields_ = [("scope", C.c_int32), ("dense_form", C.c_int32), ("refine_steps", C.c_int32),
                 ("jacobi_max_sweeps", C.c_int32), ("inband_rel", C.c_double),
                 ("eig_method", C.c_int32), ("checkpoint", C.c_int32), ("refine_cluster", C.c_int32), ("s_format", C.c_int32),
-                ("reserved", C.c_int32 * 4)]
+                ("sample_x", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 class rtcur_s_compressed(C.Structure):
@@ -119,13 +120,14 @@ EIG_TRIDIAGONAL, EIG_JACOBI = 0, 1
 
 def make_options(scope=SCOPE_SAMPLED, dense_form=FORM_FP32, refine_steps=2, jacobi_max_sweeps=30,
                  inband_rel=1e-6, eig_method=EIG_TRIDIAGONAL, checkpoint=0, refine_cluster=0,
-                 s_format=S_DENSE):
+                 s_format=S_DENSE, sample_x=SAMPLE_X_FP32):
     o = rtcur_options()
     o.scope, o.dense_form, o.refine_steps = scope, dense_form, refine_steps
     o.jacobi_max_sweeps, o.inband_rel, o.eig_method = jacobi_max_sweeps, inband_rel, eig_method
     o.checkpoint = checkpoint
     o.refine_cluster = refine_cluster
     o.s_format = s_format
+    o.sample_x = sample_x
     return o
 
 

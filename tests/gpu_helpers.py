@@ -40,3 +40,32 @@ def support_mismatch(S_gpu, ref, X, band_rel=1e-6):
     band = np.abs(np.abs(D) - zeta) <= band_rel * zeta
     diff = (S_gpu != 0) != (ref["S"] != 0)
     return int(np.count_nonzero(diff & band)), int(np.count_nonzero(diff & ~band))
+
+
+def trajectory_sensitivity(monkeypatch, X, p, sets, variant, ref, max_iter, rel=1e-7, seed=5):
+    """How far the oracle's own solve moves when every evaluation of L^(k) on the sample is
+    perturbed by a relative ``rel`` (seeded noise; 1e-7 is the size of an FP32 evaluation error):
+    the conditioning of the whole trajectory, from the oracle alone. Returns (relative Frobenius
+    change of the final L, largest absolute change of e^(k)); the solve ``ref`` is the unperturbed
+    one on the same X."""
+    from oracle import compare as CMP
+    rng = np.random.default_rng(seed)
+    es, ef = O.RTCURState.eval_subtensor, O.RTCURState.eval_fibers
+
+    def jitter(a):
+        return a * (1.0 + rel * rng.standard_normal(a.shape))
+    monkeypatch.setattr(O.RTCURState, "eval_subtensor", lambda self, I: jitter(es(self, I)))
+    monkeypatch.setattr(O.RTCURState, "eval_fibers", lambda self, d, i, J: jitter(ef(self, d, i, J)))
+    try:
+        pert = O.rtcur(X, p.ranks, sets, p.zeta0, p.gamma, p.tol, max_iter, variant,
+                       keep_full="L" in ref)
+    finally:
+        monkeypatch.undo()
+    n = min(len(pert["hist"]["e"]), len(ref["hist"]["e"]))
+    de = float(np.max(np.abs(np.asarray(pert["hist"]["e"][:n]) - np.asarray(ref["hist"]["e"][:n]))))
+    if "L" in ref:
+        dL = CMP.rel_fro(pert["L"], ref["L"])
+    else:  # compare the Tucker states on a seeded grid (no full tensor)
+        G = CMP.entry_groups(p.dims, n_slabs=0)[0]
+        dL = CMP.rel_fro(pert["state"].eval_subtensor(G), ref["state"].eval_subtensor(G))
+    return dL, de

@@ -28,6 +28,8 @@ from oracle import rtcur_oracle as O
 from paper_2108_10448_gb300 import rtcur as rt
 from paper_2108_10448_gb300 import synth
 
+from gpu_helpers import trajectory_sensitivity
+
 pytestmark = pytest.mark.gpu
 
 
@@ -103,25 +105,6 @@ def test_800cubed_full_scope_matches_oracle(big, variant, parity_log):
     assert fl["unexplained"] == 0, fl
 
 
-def _trajectory_sensitivity(monkeypatch, p, sets, variant, ref, rel=1e-7, seed=5):
-    """How far the oracle's own final L moves when every evaluation of L^(k) on the sample is
-    perturbed by a relative ``rel`` (seeded noise; 1e-7 is the size of an FP32 evaluation error):
-    the conditioning of the whole trajectory, from the oracle alone."""
-    rng = np.random.default_rng(seed)
-    es, ef = O.RTCURState.eval_subtensor, O.RTCURState.eval_fibers
-
-    def jitter(a):
-        return a * (1.0 + rel * rng.standard_normal(a.shape))
-    monkeypatch.setattr(O.RTCURState, "eval_subtensor", lambda self, I: jitter(es(self, I)))
-    monkeypatch.setattr(O.RTCURState, "eval_fibers", lambda self, d, i, J: jitter(ef(self, d, i, J)))
-    try:
-        pert = O.rtcur(p.X, p.ranks, sets, p.zeta0, p.gamma, p.tol, 100, variant, keep_full=True)
-    finally:
-        monkeypatch.undo()
-    assert pert["iters"] == ref["iters"]
-    return CMP.rel_fro(pert["L"], ref["L"])
-
-
 @pytest.mark.parametrize("variant", ["F", "R"])
 @pytest.mark.parametrize("scope", [rt.SCOPE_SAMPLED, rt.SCOPE_FULL])
 def test_100cubed_matches_oracle(variant, scope, parity_log, monkeypatch):
@@ -152,7 +135,7 @@ def test_100cubed_matches_oracle(variant, scope, parity_log, monkeypatch):
     rel = CMP.rel_fro(Lh, ref["L"])
     _, Lprev, _ = _gpu_solve(X, p, idx, variant, res.iters - 1, scope, want_S=False)
     fl = CMP.support_flips(p.X, S.cpu().numpy(), Lprev.cpu().numpy(), ref["prev_state"].full(p.dims), ref["zeta"])
-    sens = _trajectory_sensitivity(monkeypatch, p, sets, variant, ref)
+    sens, _ = trajectory_sensitivity(monkeypatch, p.X, p, sets, variant, ref, 100)
     tol_L = max(1e-5, 3.0 * sens)
     parity_log(iters=res.iters, rel_L=f"{rel:.2e}", tol_L=f"{tol_L:.2e}", sensitivity=f"{sens:.2e}",
                rel_Lstar=f"{CMP.rel_fro(Lh, p.L_star):.3f}", **fl)
