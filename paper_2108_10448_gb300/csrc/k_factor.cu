@@ -219,6 +219,19 @@ inline int nblocks(long long work) { return (int)((work + kThreads - 1) / kThrea
 
 }  // namespace
 
+// Same shared-memory carveout as the dense pass they run beside (see prepare_sample_kernels).
+cudaError_t prepare_factor_kernels() {
+  const void* fns[] = {(const void*)k_factor_B_partial, (const void*)k_factor_B_reduce,
+                       (const void*)k_core_stage, (const void*)k_table_A, (const void*)k_table_B,
+                       (const void*)k_export_cur};
+  for (const void* f : fns) {
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t launch_factor_B(const Geom& g, const Bufs& b, cudaStream_t s) {
   int blocks = 0;
   for (int i = 0; i < g.n; ++i)

@@ -750,9 +750,12 @@ __global__ void __launch_bounds__(kJacThreads, 1) k_eig_tri(Geom g, Bufs b) {
 }
 
 // ------------------------------------------------------------------ 3. FP64 refinement
+// Cluster-wide barrier that also publishes this CTA's global-memory writes to the cluster: the
+// arrive has release and the wait acquire semantics at cluster scope, so writes before it are
+// visible to every thread of the cluster after it (no GPU-scope fence, whose write
+// acknowledgements are slow while the concurrent dense pass saturates the memory system).
 __device__ void cluster_barrier() {
-  __threadfence();
-  cg::this_cluster().sync();
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
 }
 
 // Shared-memory layout of k_refine (doubles first): own rows of M, the full m x r panels X1, Yw
@@ -1494,6 +1497,14 @@ constexpr size_t kFullSmem = sizeof(float) * 3 * kFullMaxN * kFullLd;
 constexpr size_t kTriSmem = sizeof(float) * 3 * kTriMax * kTriLd;
 
 cudaError_t prepare_jacobi(size_t smem) {
+  // same shared-memory carveout as the dense pass these kernels run beside
+  const void* fns[] = {(const void*)k_gram, (const void*)k_jacobi, (const void*)k_jacobi_full,
+                       (const void*)k_eig_tri, (const void*)k_refine};
+  for (const void* f : fns) {
+    cudaError_t e0 = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                          cudaSharedmemCarveoutMaxShared);
+    if (e0 != cudaSuccess) return e0;
+  }
   cudaError_t e = raise_smem_limit((const void*)k_jacobi, (size_t)(smem));
   if (e != cudaSuccess) return e;
   e = raise_smem_limit((const void*)k_eig_tri, (size_t)(kTriSmem));
