@@ -196,14 +196,7 @@ __device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned pari
       : "memory");
   return ok != 0;
 }
-// The tile loop's wait: the default bound, or `polls` non-blocking tests when the caller set a
-// shorter limit (rtcur_set_wait_limit). The drain after a timeout always keeps the default bound.
-__device__ __forceinline__ bool mbar_wait_tile(unsigned long long* bar, unsigned parity, long long polls) {
-  if (polls <= 0) return mbar_wait_bounded(bar, parity);
-  for (long long i = 0; i < polls; ++i)
-    if (mbar_test(bar, parity)) return true;
-  return false;
-}
+
 // 1-D bulk copy of streamed data with an L2 evict-first policy: the tensor passes through L2
 // once, so it should not push out the small working set of the concurrent sampled chain.
 __device__ __forceinline__ void bulk_g2s_stream(void* dst, const void* src, unsigned bytes,
@@ -368,6 +361,16 @@ __global__ void __launch_bounds__(1024, 1) k_dense_tma(Geom g, Bufs b, int tr, i
     tq0 = stride + (long long)atomicAdd(b.ticket + TK_DTILE, 1u);
     tq1 = stride + (long long)atomicAdd(b.ticket + TK_DTILE, 1u);
   }
+  if (polls > 0) {
+    // a caller-set bound (rtcur_set_wait_limit): the launch's first wait makes `polls`
+    // non-blocking tests and gives up if its copy has not landed by then. The tile loop below
+    // then waits for that copy with the default bound and stops, and the drain completes the rest.
+    // Kept out of the loop, whose code stays that of the default bound.
+    bool ok = (blockIdx.x >= ntiles);
+    for (long long i = 0; i < polls && !ok; ++i) ok = mbar_test(&full[0], 0u);
+    if (!ok) abort_flag = 1;
+    __syncthreads();
+  }
   int it = 0;
   // static modes: tile t = CTA + it grid, known before the wait; MODE 3 reads it from the stage
   for (long long t = blockIdx.x; kDyn || t < ntiles; t += gridDim.x, ++it) {
@@ -379,7 +382,7 @@ __global__ void __launch_bounds__(1024, 1) k_dense_tma(Geom g, Bufs b, int tr, i
       tq0 = tq1;
       tq1 = stride + (long long)atomicAdd(b.ticket + TK_DTILE, 1u);
     }
-    if (!mbar_wait_tile(&full[s], par, polls)) {
+    if (!mbar_wait_bounded(&full[s], par)) {
       abort_flag = 1;
     } else if (threadIdx.x == 0) {
 #pragma unroll
