@@ -105,7 +105,10 @@ typedef struct rtcur_options {
                                 suit many concurrent problems (the batched form) */
   int32_t s_format;          /* RTCUR_S_*: format of S in the FULL scope; default DENSE */
   int32_t sample_x;          /* RTCUR_SAMPLE_X_*: what the sampled step reads X from; default FP32 */
-  int32_t reserved[3];       /* must be zero */
+  int32_t dense_ctas;        /* persistent CTAs of the FULL scope's dense pass, one per SM; 0 = auto
+                                (144 of the 152 SMs, leaving room for the concurrent sampled
+                                chain), else 1..1024 */
+  int32_t reserved[2];       /* must be zero */
 } rtcur_options;
 
 /* Compressed S^(k) (s_format COMPRESSED), in device memory owned by the plan and overwritten by

@@ -263,7 +263,7 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
   o.inband_rel = 1e-6;
   if (opt) {
     o = *opt;
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 2; ++i)
       if (o.reserved[i] != 0) return fail(nullptr, RTCUR_EINVAL, "options.reserved must be zero");
     if (o.refine_steps == 0 && o.jacobi_max_sweeps == 0 && o.inband_rel == 0.0) {
       o.refine_steps = 2; o.jacobi_max_sweeps = 30; o.inband_rel = 1e-6;
@@ -284,6 +284,7 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
     return fail(nullptr, RTCUR_EINVAL, "s_format must be DENSE (0) or COMPRESSED (1)");
   if (o.s_format == RTCUR_S_COMPRESSED && (o.scope != RTCUR_SCOPE_FULL || o.dense_form != RTCUR_FORM_FP32))
     return fail(nullptr, RTCUR_EINVAL, "s_format COMPRESSED needs the FULL scope and dense_form FP32");
+  if (o.dense_ctas < 0 || o.dense_ctas > 1024) return fail(nullptr, RTCUR_EINVAL, "dense_ctas must be in [0, 1024]");
   if (o.sample_x != RTCUR_SAMPLE_X_FP32 && o.sample_x != RTCUR_SAMPLE_X_BF16)
     return fail(nullptr, RTCUR_EINVAL, "sample_x must be FP32 (0) or BF16 (1)");
   if (o.sample_x == RTCUR_SAMPLE_X_BF16 && o.checkpoint > 0)
@@ -318,7 +319,7 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
   g.max_sweeps = o.jacobi_max_sweeps;
   g.warm_start = 0;
   g.eig_method = o.eig_method;
-  g.dense_ctas = 0;
+  g.dense_ctas = o.dense_ctas;
   g.gamma = gamma;
   g.tol = tol;
   g.inband = o.inband_rel;

@@ -25,7 +25,7 @@ class rtcur_options(C.Structure):
     _fields_ = [("scope", C.c_int32), ("dense_form", C.c_int32), ("refine_steps", C.c_int32),
                 ("jacobi_max_sweeps", C.c_int32), ("inband_rel", C.c_double),
                 ("eig_method", C.c_int32), ("checkpoint", C.c_int32), ("refine_cluster", C.c_int32), ("s_format", C.c_int32),
-                ("sample_x", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("sample_x", C.c_int32), ("dense_ctas", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class rtcur_s_compressed(C.Structure):
@@ -120,7 +120,7 @@ EIG_TRIDIAGONAL, EIG_JACOBI = 0, 1
 
 def make_options(scope=SCOPE_SAMPLED, dense_form=FORM_FP32, refine_steps=2, jacobi_max_sweeps=30,
                  inband_rel=1e-6, eig_method=EIG_TRIDIAGONAL, checkpoint=0, refine_cluster=0,
-                 s_format=S_DENSE, sample_x=SAMPLE_X_FP32):
+                 s_format=S_DENSE, sample_x=SAMPLE_X_FP32, dense_ctas=0):
     o = rtcur_options()
     o.scope, o.dense_form, o.refine_steps = scope, dense_form, refine_steps
     o.jacobi_max_sweeps, o.inband_rel, o.eig_method = jacobi_max_sweeps, inband_rel, eig_method
@@ -128,6 +128,7 @@ def make_options(scope=SCOPE_SAMPLED, dense_form=FORM_FP32, refine_steps=2, jaco
     o.refine_cluster = refine_cluster
     o.s_format = s_format
     o.sample_x = sample_x
+    o.dense_ctas = dense_ctas
     return o
 
 

@@ -32,6 +32,27 @@ def rel_fro(a, b):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
+def flip_counts(p, sets, variant, ref, S, scope=None, extra=0.0, max_iter=None, **opt):
+    """Support differences of a whole-tensor GPU S^(k) against the oracle's, as in-band /
+    L-explained / unexplained counts (oracle.compare.support_flips). L_gpu^(k-1) comes from the
+    same deterministic solve stopped one iteration earlier (only when there is a difference
+    outside the band to explain). ``extra`` widens the L-explained test by a form's evaluation
+    bound."""
+    from oracle import compare as CMP
+    Lor = ref["prev_state"].full(p.dims)
+    fl = CMP.support_flips(p.X, S, Lor, Lor, ref["zeta"], extra=extra)
+    if fl["flips"] > fl["inband"]:
+        if ref["iters"] > 1:
+            kw = dict(opt)
+            if scope is not None:
+                kw["scope"] = scope
+            _, Lprev, _ = run_gpu(p, sets, variant, max_iter=ref["iters"] - 1, want_S=False, **kw)
+        else:
+            Lprev = np.zeros_like(Lor)
+        fl = CMP.support_flips(p.X, S, Lprev, Lor, ref["zeta"], extra=extra)
+    return fl
+
+
 def support_mismatch(S_gpu, ref, X, band_rel=1e-6):
     """Support differences between the GPU's S^(k) and the oracle's, split into entries inside
     the band ||X - L^(k-1)| - zeta| <= band_rel * zeta (allowed) and outside it (not allowed)."""

@@ -58,7 +58,7 @@ def test_create_rejects_invalid_arguments(lib, kw, msg):
 def test_options_reserved_must_be_zero(lib):
     from paper_2108_10448_gb300 import rtcur as rt
     o = rt.make_options()
-    o.reserved[2] = 1
+    o.reserved[1] = 1
     with pytest.raises(rt.RTCURError) as ei:
         rt.rtcur_create([8, 8, 8], [2, 2, 2], [4, 4, 4], [8, 8, 8], 1.0, 0.7, 1e-5, 5, 0, o)
     assert ei.value.status == rt.EINVAL

@@ -57,6 +57,31 @@ def test_form_matches_fp32_form(form, shape):
     assert diff.sum() <= MAXFRAC[form] * diff.size
 
 
+@pytest.mark.parametrize("form", [rt.FORM_FP32_PLAIN, rt.FORM_BF16, rt.FORM_TF32])
+def test_form_matches_oracle(form, parity_log):
+    """Each form against the FP64 oracle itself (not only against the FP32 form): the same
+    iterates, and S^(k)'s support differences in band / L-explained (the FP32 L^(k-1) difference
+    plus the form's evaluation band) / unexplained, the last required to be 0."""
+    from oracle import compare as CMP
+    from oracle import rtcur_oracle as O
+    from gpu_helpers import rel_fro
+    dims, ranks, seed = SHAPES[0]
+    p = synth.make_tucker_problem(dims, ranks, 0.1, 3, seed=seed, max_iter=40)
+    sets = synth.draw_index_sets(p.dims, p.m, p.q, seed=seed)
+    ref = O.rtcur(p.X, p.ranks, sets, p.zeta0, p.gamma, p.tol, 40, "F", keep_full=True)
+    res, L, S = run_gpu(p, sets, "F", scope=rt.SCOPE_FULL, max_iter=40, dense_form=form)
+    assert res.iters == ref["iters"]
+    np.testing.assert_allclose(res.e_hist, ref["hist"]["e"], rtol=1e-4, atol=5e-8)
+    rel = rel_fro(L, ref["L"])
+    assert rel <= 1e-5
+    _, Lprev, _ = run_gpu(p, sets, "F", scope=rt.SCOPE_FULL, max_iter=res.iters - 1, want_S=False,
+                          dense_form=form)
+    fl = CMP.support_flips(p.X, S, Lprev, ref["prev_state"].full(p.dims), ref["zeta"],
+                           extra=BAND[form] * np.max(np.abs(ref["L"])))
+    parity_log(form=form, iters=res.iters, rel_L=f"{rel:.2e}", **fl)
+    assert fl["unexplained"] == 0, fl
+
+
 def test_tensor_core_forms_reject_unsupported_shapes():
     # d_n % 4 != 0 (TMA row stride), d_n > 1024, BF16 with 3 r_n > 16, TF32 with r_n > 8
     for dims, ranks, form in (([20, 20, 30], [2, 2, 2], rt.FORM_BF16),
