@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched-form comparison (64 uneven problems)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint timing")
+    ap.add_argument("--quick", action="store_true",
+                    help="only the timed iterations and the dense kernel's roofline (for profiling runs)")
     return ap.parse_args()
 
 
@@ -526,6 +528,14 @@ def run_ours(a, rank, world):
                 "frac_of_nominal": achieved / NOMINAL_HBM_GBS, "nominal_peak": NOMINAL_HBM_GBS,
                 "iteration_frac": alg_bytes / (ms / K / 1e3) / 1e9 / peak,
                 "algorithmic_bytes_per_launch": alg_bytes}
+    if a.quick:
+        rt.rtcur_destroy(plan)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
+                              "steps": K, "warmup": W, "ms_per_step": ms / K, "higher_is_better": True,
+                              "quick": True, "config": workload_config(a, p, world), "roofline": roof}),
+                  flush=True)
+        return
     # --- time to tolerance: whole solve from X resident, one graph launch; median of 5 after 2 ---
     ttt_ms, ttts, res = solve_timed(rt, plan, X, idx, L, S, sh, stream, max_iter)
     parity_gpu = {}

@@ -348,7 +348,7 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
     g.offY[i] = oY; oY += (long long)g.q[i] * g.r[i];
     g.offR[i] = oR; oR += g.r[i];
     g.offL[i] = oL; oL += g.m[i];
-    long long c = (g.q[i] + 31) / 32;
+    long long c = (g.q[i] + RT_BCHUNK - 1) / RT_BCHUNK;
     if (c > nch) nch = c;
   }
   g.sumB = oB;

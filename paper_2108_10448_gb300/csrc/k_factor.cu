@@ -11,7 +11,7 @@
 namespace {
 
 constexpr int kThreads = 128;
-constexpr int kChunk = 32;   // b-columns per split-K partial of B_i = C_i Y_i
+constexpr int kChunk = RT_BCHUNK;  // b-columns per split-K partial of B_i = C_i Y_i
 
 // B partials: block -> (mode, t-block, chunk); thread -> row t.
 __global__ void __launch_bounds__(kThreads) k_factor_B_partial(Geom g, Bufs b) {
@@ -64,7 +64,10 @@ __global__ void __launch_bounds__(kThreads) k_factor_B_reduce(Geom g, Bufs b) {
 
 // One stage of G = R x_{n-1} Q^T ... x_0 Q^T (modes contracted from last to first).
 // Before stage s the modes j' > j = n-1-s already have size r, the others m. Q_j (m_j x r_j,
-// FP64) is staged in shared memory; each thread forms one output as an FP64 dot product.
+// FP64) is staged in shared memory; each output is an FP64 dot product of length m_j split over a
+// quad of lanes (terms a = ql mod 4), which quarters its dependent chain and quadruples the warps
+// of the small later stages.
+constexpr int kCoreOut = kThreads / 4;  // outputs per block
 __global__ void __launch_bounds__(kThreads) k_core_stage(Geom g, Bufs b, int s, long long nout) {
   TL_BEGIN();
   __shared__ double Qs[RT_MAXM * RT_MAXR];
@@ -75,8 +78,10 @@ __global__ void __launch_bounds__(kThreads) k_core_stage(Geom g, Bufs b, int s, 
   const double* Q = b.Qr + g.offQ[j];
   for (int t = threadIdx.x; t < mj * r; t += blockDim.x) Qs[t] = Q[t];
   __syncthreads();
-  long long o = (long long)blockIdx.x * kThreads + threadIdx.x;
-  if (o >= nout) return;
+  const int ql = threadIdx.x & 3;
+  long long o = (long long)blockIdx.x * kCoreOut + (threadIdx.x >> 2);
+  const bool act = o < nout;  // whole quads are active or not
+  if (!act) o = 0;
   int shp_in[RT_MAXN], shp_out[RT_MAXN];
   for (int l = 0; l < n; ++l) {
     shp_in[l] = (l > j) ? g.r[l] : g.m[l];
@@ -99,17 +104,23 @@ __global__ void __launch_bounds__(kThreads) k_core_stage(Geom g, Bufs b, int s, 
   }
   const int cj = co[j];
   double acc = 0.0;
-  if (s == 0) {
-    const float* R = b.XS;  // segment 0
-    for (int a = 0; a < mj; ++a) acc = fma((double)R[base + a * strj], Qs[a * r + cj], acc);
-  } else {
-    const double* Zin = b.Z[(s - 1) & 1];
-    for (int a = 0; a < mj; ++a) acc = fma(Zin[base + a * strj], Qs[a * r + cj], acc);
+  if (act) {
+    if (s == 0) {
+      const float* R = b.XS;  // segment 0
+      for (int a = ql; a < mj; a += 4) acc = fma((double)R[base + a * strj], Qs[a * r + cj], acc);
+    } else {
+      const double* Zin = b.Z[(s - 1) & 1];
+      for (int a = ql; a < mj; a += 4) acc = fma(Zin[base + a * strj], Qs[a * r + cj], acc);
+    }
   }
-  if (s == n - 1) {
-    b.G[(b.st->k + 1) & 1][o] = (float)acc;
-  } else {
-    b.Z[s & 1][o] = acc;
+  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+  if (act && ql == 0) {
+    if (s == n - 1) {
+      b.G[(b.st->k + 1) & 1][o] = (float)acc;
+    } else {
+      b.Z[s & 1][o] = acc;
+    }
   }
   TL_END(8);
 }
@@ -248,7 +259,7 @@ cudaError_t launch_core(const Geom& g, const Bufs& b, cudaStream_t s) {
     int j = g.n - 1 - st;
     long long nout = 1;
     for (int l = 0; l < g.n; ++l) nout *= (l >= j) ? g.r[l] : g.m[l];
-    k_core_stage<<<nblocks(nout), kThreads, 0, s>>>(g, b, st, nout);
+    k_core_stage<<<(int)((nout + kCoreOut - 1) / kCoreOut), kThreads, 0, s>>>(g, b, st, nout);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -43,7 +43,10 @@ __device__ __forceinline__ const long long* set_of(const Geom& g, const Bufs& b)
 }
 
 // ------------------------------------------------------------------ 1. FP64 Gram matrix
-__global__ void __launch_bounds__(kGramTile * kGramTile) k_gram(Geom g, Bufs b) {
+// One 8 x 8 tile of M_i = W_i W_i^T per block; each entry's FP64 dot product is split over a quad
+// of lanes (columns c = ql mod 4), so a block runs 8 warps and each FP64 chain is a quarter as long.
+constexpr int kGramThreads = 4 * kGramTile * kGramTile;
+__global__ void __launch_bounds__(kGramThreads) k_gram(Geom g, Bufs b) {
   TL_BEGIN();
   __shared__ float wa[kGramTile][kGramChunk + 1];
   __shared__ float wb[kGramTile][kGramChunk + 1];
@@ -61,7 +64,8 @@ __global__ void __launch_bounds__(kGramTile * kGramTile) k_gram(Geom g, Bufs b) 
   int tb = blk - ta * (ta + 1) / 2;  // tb <= ta
   const long long* set = set_of(g, b);
   const int m = g.m[i], q = g.q[i];
-  const int ty = threadIdx.x / kGramTile, tx = threadIdx.x % kGramTile;
+  const int o = threadIdx.x >> 2, ql = threadIdx.x & 3;  // entry of the tile, lane of its quad
+  const int ty = o / kGramTile, tx = o % kGramTile;
   const int a0 = ta * kGramTile, b0 = tb * kGramTile;
   double acc = 0.0;
   for (int c0 = 0; c0 < q; c0 += kGramChunk) {
@@ -72,11 +76,13 @@ __global__ void __launch_bounds__(kGramTile * kGramTile) k_gram(Geom g, Bufs b) 
       wb[rr][cc] = (b0 + rr < m) ? w_entry(g, b, set, i, b0 + rr, c0 + cc) : 0.f;
     }
     __syncthreads();
-    for (int cc = 0; cc < cn; ++cc) acc = fma((double)wa[ty][cc], (double)wb[tx][cc], acc);
+    for (int cc = ql; cc < cn; cc += 4) acc = fma((double)wa[ty][cc], (double)wb[tx][cc], acc);
     __syncthreads();
   }
+  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
   int ra = a0 + ty, rb = b0 + tx;
-  if (ra < m && rb < m) {
+  if (ql == 0 && ra < m && rb < m) {
     double* M = b.gram + g.offM[i];
     M[(long long)ra * m + rb] = acc;
     M[(long long)rb * m + ra] = acc;
@@ -1489,7 +1495,7 @@ cudaError_t launch_gram(const Geom& g, const Bufs& b, cudaStream_t s) {
     int nt = (g.m[i] + kGramTile - 1) / kGramTile;
     blocks += nt * (nt + 1) / 2;
   }
-  k_gram<<<blocks, kGramTile * kGramTile, 0, s>>>(g, b);
+  k_gram<<<blocks, kGramThreads, 0, s>>>(g, b);
   return cudaGetLastError();
 }
 

@@ -45,6 +45,43 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return t;
 }
 
+// Block-wide sums of N values at once (kThreads threads): the same shuffle tree and the same
+// warp order as block_sum, so each sum is bit-identical to N separate block_sum calls, but with one
+// barrier instead of 2N. Sum j is returned in thread j (j < N).
+template <int N>
+__device__ __forceinline__ double block_sum_n(const double (&v)[N], double* sh) {
+  double r[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    double x = v[j];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    r[j] = x;
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+#pragma unroll
+    for (int j = 0; j < N; ++j) sh[j * (kThreads / 32) + w] = r[j];
+  }
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < N)
+    for (int i = 0; i < kThreads / 32; ++i) t += sh[threadIdx.x * (kThreads / 32) + i];
+  return t;
+}
+
+// Sums of slots 0..N-1 over the first `nb` block partials (fixed order per thread, then the block
+// sums), sum j in thread j.
+template <int N>
+__device__ __forceinline__ double sum_partials_n(const double* part, int nb, double* sh) {
+  double acc[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) acc[j] = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x)
+#pragma unroll
+    for (int j = 0; j < N; ++j) acc[j] += part[i * RT_RED_SLOTS + j];
+  return block_sum_n<N>(acc, sh);
+}
+
 // Sum of slot `slot` over the first `nb` block partials, by the whole block (fixed order per
 // thread, then a block sum); result valid in thread 0.
 __device__ __forceinline__ double sum_partials(const double* part, int nb, int slot, double* sh) {
@@ -151,7 +188,7 @@ __device__ __forceinline__ int segment_of(const Geom& g, long long e) {
 
 __global__ void __launch_bounds__(kThreads) k_sample_ht(Geom g, Bufs b) {
   TL_BEGIN();
-  __shared__ double sh[kThreads / 32];
+  __shared__ double sh[8 * (kThreads / 32) + 16];  // block_sum_n<8> and the segment sums
   const State* st = b.st;
   const int k = st->k;
   const int cur = k & 1;
@@ -215,29 +252,24 @@ __global__ void __launch_bounds__(kThreads) k_sample_ht(Geom g, Bufs b) {
       if (s == seg) den[s] += xx;
   }
   double* part = b.red + (size_t)TK_SAMPLE * kMaxRedBlocks * RT_RED_SLOTS;
-  double tot;
+  {
+    double v[8];
 #pragma unroll
-  for (int s = 0; s < RT_MAXN + 1; ++s) {
-    tot = block_sum((double)den[s], sh);
-    if (threadIdx.x == 0) part[blockIdx.x * RT_RED_SLOTS + s] = tot;
+    for (int s = 0; s < RT_MAXN + 1; ++s) v[s] = (double)den[s];
+    v[5] = (double)nnz;
+    v[6] = (double)inb;
+    v[7] = (double)bad;
+    const double tot = block_sum_n<8>(v, sh);
+    if (threadIdx.x < 8) part[blockIdx.x * RT_RED_SLOTS + threadIdx.x] = tot;
   }
-  tot = block_sum((double)nnz, sh);
-  if (threadIdx.x == 0) part[blockIdx.x * RT_RED_SLOTS + 5] = tot;
-  tot = block_sum((double)inb, sh);
-  if (threadIdx.x == 0) part[blockIdx.x * RT_RED_SLOTS + 6] = tot;
-  tot = block_sum((double)bad, sh);
-  if (threadIdx.x == 0) part[blockIdx.x * RT_RED_SLOTS + 7] = tot;
   if (last_block_arrive(b.ticket + TK_SAMPLE)) {
     State* w = b.st;
-    for (int slot = 0; slot < 8; ++slot) {
-      double acc = sum_partials(part, gridDim.x, slot, sh);
-      if (threadIdx.x == 0) {
-        if (slot < RT_MAXN + 1) w->den[slot] = acc;
-        if (slot == 5) w->nnz_s = (long long)acc;
-        if (slot == 6) w->inband_s = (long long)acc;
-        if (slot == 7 && acc > 0.0) w->err = -4;  // RTCUR_ENONFINITE
-      }
-    }
+    const double acc = sum_partials_n<8>(part, gridDim.x, sh);  // slot j in thread j
+    const int slot = threadIdx.x;
+    if (slot < RT_MAXN + 1) w->den[slot] = acc;
+    if (slot == 5) w->nnz_s = (long long)acc;
+    if (slot == 6) w->inband_s = (long long)acc;
+    if (slot == 7 && acc > 0.0) w->err = -4;  // RTCUR_ENONFINITE
     if (threadIdx.x == 0) {
       w->jsweeps = 0;
       b.ticket[TK_SAMPLE] = 0u;
@@ -248,7 +280,7 @@ __global__ void __launch_bounds__(kThreads) k_sample_ht(Geom g, Bufs b) {
 
 __global__ void __launch_bounds__(kThreads) k_sample_err(Geom g, Bufs b) {
   TL_BEGIN();
-  __shared__ double sh[kThreads / 32];
+  __shared__ double sh[8 * (kThreads / 32) + 16];  // block_sum_n<8> and the segment sums
   const State* st = b.st;
   const int k = st->k;
   const int nxt = (k + 1) & 1;
@@ -270,23 +302,26 @@ __global__ void __launch_bounds__(kThreads) k_sample_err(Geom g, Bufs b) {
       if (s == seg) num[s] += ee;
   }
   double* part = b.red + (size_t)TK_ERR * kMaxRedBlocks * RT_RED_SLOTS;
+  {
+    double v[RT_MAXN + 1];
 #pragma unroll
-  for (int s = 0; s < RT_MAXN + 1; ++s) {
-    double tot = block_sum((double)num[s], sh);
-    if (threadIdx.x == 0) part[blockIdx.x * RT_RED_SLOTS + s] = tot;
+    for (int s = 0; s < RT_MAXN + 1; ++s) v[s] = (double)num[s];
+    const double tot = block_sum_n<RT_MAXN + 1>(v, sh);
+    if (threadIdx.x < RT_MAXN + 1) part[blockIdx.x * RT_RED_SLOTS + threadIdx.x] = tot;
   }
   if (last_block_arrive(b.ticket + TK_ERR)) {
     State* w = b.st;
-    double sn = 0.0, sd = 0.0;
-    for (int s = 0; s <= g.n; ++s) {
-      double acc = sum_partials(part, gridDim.x, s, sh);
-      if (threadIdx.x == 0) {
-        w->num[s] = acc;
-        sn += sqrt(acc);
+    const double acc = sum_partials_n<RT_MAXN + 1>(part, gridDim.x, sh);  // segment j in thread j
+    if (threadIdx.x <= g.n) sh[64 + threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sn = 0.0, sd = 0.0;
+      for (int s = 0; s <= g.n; ++s) {
+        const double a = sh[64 + s];
+        w->num[s] = a;
+        sn += sqrt(a);
         sd += sqrt(w->den[s]);
       }
-    }
-    if (threadIdx.x == 0) {
       w->e_stage = (sd > 0.0) ? sn / sd : 0.0;
       b.ticket[TK_ERR] = 0u;
     }

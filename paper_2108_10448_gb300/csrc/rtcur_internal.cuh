@@ -24,6 +24,7 @@
 #define RT_MAXM 192      // cap on |I_i| (the FP32 Jacobi keeps M and V in shared memory)
 #define RT_MAXQ 4096     // cap on |J_i|
 #define RT_RED_SLOTS 16  // doubles per block in reduction partials
+#define RT_BCHUNK 8      // J_i columns per split-K partial of B_i = C_i Y_i
 
 struct Geom {
   int n;
