@@ -641,6 +641,15 @@ def run_ours(a, rank, world):
             rt.rtcur_destroy(sp_)
             sampled_ttt[v] = {"ms": v_ms, "runs_ms": v_ts, "iters": vres.iters, "e": vres.e,
                               "status": vres.status}
+            # the same solve with the sampled step reading a BF16 copy of X (option sample_x)
+            bp = rt.rtcur_create(p.dims, p.ranks, p.m, p.q, p.zeta0, p.gamma, p.tol, max_iter,
+                                 rt.VARIANT_R if v == "R" else rt.VARIANT_F,
+                                 rt.make_options(scope=rt.SCOPE_SAMPLED, sample_x=rt.SAMPLE_X_BF16))
+            b_ms, _, bres = solve_timed(rt, bp, X, synth.pack_index_sets(v_sets), L, None, sh, stream,
+                                        max_iter, reps=4, skip=1)
+            rt.rtcur_destroy(bp)
+            sampled_ttt[v]["sample_x_bf16"] = {"ms": b_ms, "iters": bres.iters, "e": bres.e,
+                                               "note": "includes the BF16 copy of X made by rtcur_begin"}
     # --- end to end through the C ABI from pinned host buffers ---
     Xh = torch.from_numpy(p.X).pin_memory()
     Lh = torch.empty_like(Xh).pin_memory()

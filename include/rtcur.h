@@ -106,8 +106,8 @@ typedef struct rtcur_options {
   int32_t s_format;          /* RTCUR_S_*: format of S in the FULL scope; default DENSE */
   int32_t sample_x;          /* RTCUR_SAMPLE_X_*: what the sampled step reads X from; default FP32 */
   int32_t dense_ctas;        /* persistent CTAs of the FULL scope's dense pass, one per SM; 0 = auto
-                                (144 of the 152 SMs, leaving room for the concurrent sampled
-                                chain), else 1..1024 */
+                                (148 of the 152 SMs for the FP32 pass, 144 for the tensor-core
+                                forms, leaving room for the concurrent sampled chain), else 1..1024 */
   int32_t reserved[2];       /* must be zero */
 } rtcur_options;
 

@@ -425,11 +425,9 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
   AL(b.gram, oM);
   AL(b.jV, oM);
   AL(b.jL, oL);
-  AL(b.X1, oQ);
   AL(b.Qr, oQ);
   AL(b.sig, oR);
   AL(b.Y, oY);
-  AL(b.ework, 3 * oQ + 3 * 16 * RT_MAXN);
   AL(b.warm, RT_MAXN);
   AL(b.wratio, RT_MAXN);
   AL(b.Bpart, g.nchunk * g.sumB);

@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(512) k_dense_fp32(Geom g, Bufs b) {
 }
 
 // ---------------------------------------------------------------- TMA-fed fused pass
-// Persistent CTAs (144 of the 152 SMs, one CTA per SM by shared-memory footprint, so a few SMs
+// Persistent CTAs (148 of the 152 SMs, one CTA per SM by shared-memory footprint, so a few SMs
 // stay free for the concurrent sampled chain). Each CTA streams tiles of `tr` whole rows of X
 // (tr * d_n floats, ~32 KB) into a kStages-deep shared-memory ring with 1-D cp.async.bulk
 // copies completed on mbarriers; one thread per float4 column computes L from its register
@@ -765,7 +765,9 @@ cudaError_t launch_dense(const Geom& g, const Bufs& b, int form, cudaStream_t s)
     size_t smem;
     if (tma_geometry(g, tr, smem, threads)) {
       long long ntiles = (g.rowsT + tr - 1) / tr;
-      int ctas = g.dense_ctas > 0 ? g.dense_ctas : 144;
+      // 148 persistent CTAs: measured best for the iteration at 800^3 (the pass alone keeps
+      // gaining up to 152, but the concurrent sampled chain then finds no room on any SM)
+      int ctas = g.dense_ctas > 0 ? g.dense_ctas : 148;
       int grid = (int)(ntiles < ctas ? ntiles : ctas);
       const int mode = (g.s_format == RTCUR_S_COMPRESSED) ? 3 : 0;
       // the compressed pass runs two row groups: twice the warps for its longer row loop, and
@@ -810,7 +812,8 @@ cudaError_t launch_materialize(const Geom& g, const Bufs& b, float* L_out, float
     size_t smem;
     if (tma_geometry(g, tr, smem, threads)) {
       long long ntiles = (g.rowsT + tr - 1) / tr;
-      int grid = (int)(ntiles < 144 ? ntiles : 144);
+      // the outputs are written after the loop, with nothing beside them: every SM
+      int grid = (int)(ntiles < 152 ? ntiles : 152);
       switch (g.rlast) {
         case 1: return tma_materialize_rn<1>(g, b, tr, smem, grid, threads, L_out, S_out, s);
         case 2: return tma_materialize_rn<2>(g, b, tr, smem, grid, threads, L_out, S_out, s);

@@ -765,8 +765,9 @@ __device__ void cluster_barrier() {
 }
 
 // Shared-memory layout of k_refine (doubles first): own rows of M, the full m x r panels X1, Yw
-// and E (re-read from global memory after each cluster barrier), the FP32 basis restricted to
-// this CTA's columns and rows, and a chunk of W columns for Y = W^T Q_r Sigma^-2.
+// and E (each CTA computes its own rows and gathers the others' from their shared memory after a
+// cluster barrier), the FP32 basis restricted to this CTA's columns and rows, and a chunk of W
+// columns for Y = W^T Q_r Sigma^-2.
 constexpr int kWChunk = 32;
 constexpr int kWarmMaxSteps = 12;  // subspace-iteration steps a warm attempt may take
 // Cold path: when the FP32 eigenvalues put lambda_r below kLowLambda lambda_1 (sigma_r / sigma_1
@@ -823,6 +824,24 @@ __device__ __forceinline__ void load_panel(double* dst, const double* src, int n
   for (int t = threadIdx.x; t < n; t += blockDim.x) dst[t] = src[t];
 }
 
+// Panel exchange through distributed shared memory. The rows of an m-row panel are split over
+// the cluster's CTAs as [m c / NCL, m (c + 1) / NCL) (row a belongs to rank owner[a]); every CTA
+// has written its own rows of the m x r panel sP (same offset in every CTA's shared memory).
+// After the cluster barrier (release / acquire at cluster scope, which orders the shared-memory
+// writes) each CTA copies the other CTAs' rows from their shared memory. A CTA may overwrite its
+// own rows again only after the next cluster barrier, and may exit only after a cluster barrier
+// that follows the last exchange.
+__device__ __forceinline__ void exchange_panel(double* sP, int m, int r, int crank,
+                                            const unsigned char* owner) {
+  cluster_barrier();
+  cg::cluster_group cl = cg::this_cluster();
+  for (int t = threadIdx.x; t < m * r; t += blockDim.x) {
+    const int c = owner[t / r];
+    if (c != crank) sP[t] = cl.map_shared_rank(sP, (unsigned)c)[t];
+  }
+  __syncthreads();
+}
+
 // mode 1: full refinement after the FP32 eigensolver (skipped for a mode whose warm attempt
 //         succeeded). mode 0: warm attempt (RTCUR-F, k >= 1): three FP64 subspace-iteration
 //         steps from the previous iteration's basis, accepted only when certified (see below).
@@ -847,14 +866,17 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
   __shared__ int order[RT_MAXR];
   __shared__ int tie;
   __shared__ float lam[RT_MAXM];
-  for (int a = tid; a < m; a += blockDim.x) lam[a] = b.jL[g.offL[i] + a];
+  __shared__ unsigned char rown[RT_MAXM];  // cluster rank that owns each panel row
+  for (int a = tid; a < m; a += blockDim.x) {
+    lam[a] = b.jL[g.offL[i] + a];
+    int c = (a * NCL) / m;
+    while (c + 1 < NCL && (m * (c + 1)) / NCL <= a) ++c;
+    while (c > 0 && (m * c) / NCL > a) --c;
+    rown[a] = (unsigned char)c;
+  }
   __syncthreads();
   const float* Xh = b.jV + g.offM[i];               // m x m, column j = vector j
   const double* M = b.gram + g.offM[i];
-  double* X1 = b.X1 + g.offQ[i];                    // m x r
-  double* Yw = b.ework + g.offQ[i];                 // m x r
-  double* E = b.ework + g.sumMR + g.offQ[i];        // m x r (rows: basis index)
-  double* Qw = b.ework + 2 * g.sumMR + g.offQ[i];   // m x r
   double* Qr = b.Qr + g.offQ[i];
   double* sig = b.sig + g.offR[i];
   double* Yout = b.Y + g.offY[i];
@@ -929,11 +951,9 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
         for (int c = ql; c < m; c += 4) acc = fma(Ma[c], sX1[c * r + j], acc);
       }
       acc = quad_sum_d(acc);
-      if (act && ql == 0) Yw[(long long)(lo + a) * r + j] = acc;
+      if (act && ql == 0) sYw[(lo + a) * r + j] = acc;
     }
-    cluster_barrier();
-    load_panel(sYw, Yw, m * r);
-    __syncthreads();
+    exchange_panel(sYw, m, r, crank, rown);
     for (int t = wid; t < r * r; t += nw) {
       int j = t / r, l = t % r;
       double acc = 0.0;
@@ -948,7 +968,10 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
         if (Gq[j * r + j] <= min_pivot * Gq[0]) chol_ok = 0;
     }
     __syncthreads();
-    if (!chol_ok) return false;
+    if (!chol_ok) {
+      cluster_barrier();  // the other CTAs may still be reading this CTA's rows of sYw
+      return false;
+    }
     for (int a = lo + tid; a < hi; a += blockDim.x) {
       double y[RT_MAXR];
 #pragma unroll
@@ -961,22 +984,16 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
       }
 #pragma unroll
       for (int j = 0; j < RT_MAXR; ++j)
-        if (j < r) X1[(long long)a * r + j] = y[j];
+        if (j < r) sX1[a * r + j] = y[j];  // own rows only: no thread reads sX1 in this phase
     }
-    cluster_barrier();
-    load_panel(sX1, X1, m * r);
-    __syncthreads();
+    exchange_panel(sX1, m, r, crank, rown);
     return true;
   };
   int oa_steps = g.refine_steps;  // Ogita-Aishima steps of the cold path
   if (mode == 0) {
-    // warm start: the previous iteration's top-r basis, then FP64 subspace iteration
-    for (int t = tid; t < own * r; t += blockDim.x) {
-      int a = lo + t / r, j = t % r;
-      X1[(long long)a * r + j] = Qr[(long long)a * r + j];
-    }
-    cluster_barrier();
-    load_panel(sX1, X1, m * r);
+    // warm start: the previous iteration's top-r basis (complete in global memory), then FP64
+    // subspace iteration
+    load_panel(sX1, Qr, m * r);
     __syncthreads();
   warm_steps:
     for (int it = 0; it < wsteps; ++it)
@@ -984,12 +1001,10 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
     wtotal += wsteps;
     oa_steps = 0;
   } else {
-  for (int t = tid; t < own * r; t += blockDim.x) {
-    int a = lo + t / r, j = t % r;
-    X1[(long long)a * r + j] = (double)Xh[(long long)a * m + top[j]];
+  for (int t = tid; t < m * r; t += blockDim.x) {
+    int a = t / r, j = t % r;
+    sX1[t] = (double)Xh[(long long)a * m + top[j]];
   }
-  cluster_barrier();
-  load_panel(sX1, X1, m * r);
   __syncthreads();
   // lambda_r below the resolution of the FP32 eigenbasis (its eigenvalues carry an absolute
   // error of about m 2^-24 lambda_1): the FP32 basis does not resolve eigenvector r from the
@@ -1020,11 +1035,9 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
         for (int c = ql; c < m; c += 4) acc = fma(Ma[c], sX1[c * r + j], acc);
       }
       acc = quad_sum_d(acc);
-      if (t < own * r && ql == 0) Yw[(long long)(lo + a) * r + j] = acc;
+      if (t < own * r && ql == 0) sYw[(lo + a) * r + j] = acc;
     }
-    cluster_barrier();
-    load_panel(sYw, Yw, m * r);
-    __syncthreads();
+    exchange_panel(sYw, m, r, crank, rown);
     // Rayleigh quotients of the current top columns (every CTA, redundantly)
     for (int j = wid; j < r; j += nw) {
       double s1 = 0.0, nn = 0.0;
@@ -1079,11 +1092,9 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
           tie = 1;
         }
       }
-      E[(long long)ii * r + j] = Eij;
+      sE[ii * r + j] = Eij;  // own basis indices (no thread reads sE in this phase)
     }
-    cluster_barrier();
-    load_panel(sE, E, m * r);
-    __syncthreads();
+    exchange_panel(sE, m, r, crank, rown);
     // S3: X1 <- X1 + Xf E on own rows (one quad per output)
     for (int t0 = tid >> 2; t0 < ((own * r + nq - 1) / nq) * nq; t0 += nq) {
       const int t = t0;
@@ -1099,11 +1110,13 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
         }
       }
       upd = quad_sum_d(upd);
-      if (act && ql == 0) X1[(long long)(lo + a) * r + j] = sX1[(lo + a) * r + j] + upd;
+      // staged in sYw (not read in this phase; the other CTAs finished reading it before the last
+      // exchange), because other threads still read sX1's own rows
+      if (act && ql == 0) sYw[(lo + a) * r + j] = sX1[(lo + a) * r + j] + upd;
     }
-    cluster_barrier();
-    load_panel(sX1, X1, m * r);
     __syncthreads();
+    for (int t = tid; t < own * r; t += blockDim.x) sX1[lo * r + t] = sYw[lo * r + t];
+    exchange_panel(sX1, m, r, crank, rown);
     PHASE_MARK(tph, "ref.step");
   }
   // Fast finish. L needs only the top-r invariant subspace: for any basis X1 of it,
@@ -1122,11 +1135,9 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
       for (int c = ql; c < m; c += 4) acc = fma(Ma[c], sX1[c * r + j], acc);
     }
     acc = quad_sum_d(acc);
-    if (act && ql == 0) Yw[(long long)(lo + a) * r + j] = acc;
+    if (act && ql == 0) sYw[(lo + a) * r + j] = acc;
   }
-  cluster_barrier();
-  load_panel(sYw, Yw, m * r);
-  __syncthreads();
+  exchange_panel(sYw, m, r, crank, rown);
   for (int t = wid; t < r * r; t += nw) {
     int j = t / r, l = t % r;
     double acc = 0.0;
@@ -1156,19 +1167,19 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
     __shared__ double wpart[3][32];
     if (lane == 0) { wpart[0][wid] = fmp; wpart[1][wid] = rsp; wpart[2][wid] = mxp; }
     __syncthreads();
+    __shared__ double cslot[3];  // this CTA's partials, read by the cluster's CTAs in rank order
     if (tid == 0) {
       double a0 = 0.0, a1 = 0.0, a2 = 0.0;
       for (int w = 0; w < nw; ++w) { a0 += wpart[0][w]; a1 += wpart[1][w]; a2 += wpart[2][w]; }
-      double* slot = b.ework + 3 * g.sumMR + (long long)(i * NCL + crank) * 3;
-      slot[0] = a0;
-      slot[1] = a1;
-      slot[2] = a2;
+      cslot[0] = a0;
+      cslot[1] = a1;
+      cslot[2] = a2;
     }
     cluster_barrier();
     if (tid == 0) {
       double a0 = 0.0, a1 = 0.0, a2 = 0.0;
       for (int c2 = 0; c2 < NCL; ++c2) {
-        const double* slot = b.ework + 3 * g.sumMR + (long long)(i * NCL + c2) * 3;
+        const double* slot = cl.map_shared_rank(cslot, (unsigned)c2);
         a0 += slot[0];
         a1 += slot[1];
         a2 += slot[2];
@@ -1270,14 +1281,12 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
 #pragma unroll
       for (int j = 0; j < RT_MAXR; ++j)
         if (j < r) {
-          Qw[(long long)a * r + j] = y[j];
+          sE[a * r + j] = y[j];  // own rows (sE is not read in this phase)
           Qr[(long long)a * r + j] = sX1[a * r + j];
         }
     }
     if (crank == 0 && tid < r) sig[tid] = wv[tid];
-    cluster_barrier();
-    load_panel(sE, Qw, m * r);  // sE holds P = X1 H^-1
-    __syncthreads();
+    exchange_panel(sE, m, r, crank, rown);  // sE holds P = X1 H^-1
     // Y = W^T P (q x r) on own columns of W
     const int blo = (q * crank) / NCL, bhi = (q * (crank + 1)) / NCL;
     for (int c0 = blo; c0 < bhi; c0 += kWChunk) {
@@ -1305,9 +1314,13 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
     }
     PHASE_MARK(tph, "ref.fast");
     TL_END(4 + 10 * mode);
+    cluster_barrier();  // no CTA leaves while another still reads its shared memory
     return;
   }
-  if (mode == 0) return;  // not certified: the eigensolver and the full refinement run
+  if (mode == 0) {  // not certified: the eigensolver and the full refinement run
+    cluster_barrier();  // no CTA leaves while another still reads its shared memory
+    return;
+  }
   // ---- exact path (H close to the SVD_r cutoff): singular vectors and the cutoff
   // F1: orthonormalise X1 (Cholesky QR in FP64)
   for (int t = wid; t < r * r; t += nw) {
@@ -1346,11 +1359,9 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
     }
 #pragma unroll
     for (int j = 0; j < RT_MAXR; ++j)
-      if (j < r) Qw[(long long)a * r + j] = y[j];
+      if (j < r) sX1[a * r + j] = y[j];  // in place: this thread alone reads and writes row a
   }
-  cluster_barrier();
-  load_panel(sX1, Qw, m * r);  // sX1 now holds Q
-  __syncthreads();
+  exchange_panel(sX1, m, r, crank, rown);  // sX1 now holds Q
   // F2: Yw = M Q on own rows (one quad per output)
   for (int t0 = tid >> 2; t0 < ((own * r + nq - 1) / nq) * nq; t0 += nq) {
     const int t = t0;
@@ -1362,11 +1373,9 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
       for (int c = ql; c < m; c += 4) acc = fma(Ma[c], sX1[c * r + j], acc);
     }
     acc = quad_sum_d(acc);
-    if (act && ql == 0) Yw[(long long)(lo + a) * r + j] = acc;
+    if (act && ql == 0) sYw[(lo + a) * r + j] = acc;
   }
-  cluster_barrier();
-  load_panel(sYw, Yw, m * r);
-  __syncthreads();
+  exchange_panel(sYw, m, r, crank, rown);
   PHASE_MARK(tph, "ref.qr+MQ");
   // F3: H = Q^T M Q (r x r), its eigenpairs by FP64 cyclic Jacobi, cutoff of SVD_r
   for (int t = wid; t < r * r; t += nw) {
@@ -1449,13 +1458,13 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
     int a = lo + t / r, j = t % r;
     double acc = 0.0;
     for (int l = 0; l < r; ++l) acc = fma(sX1[a * r + l], Yh[l * r + order[j]], acc);
-    Qr[(long long)a * r + j] = (wv[j] > 0.0) ? acc : 0.0;
+    const double qv = (wv[j] > 0.0) ? acc : 0.0;
+    Qr[(long long)a * r + j] = qv;
+    sE[a * r + j] = qv;  // own rows (sE is not read in this phase)
   }
   if (crank == 0 && tid < r) sig[tid] = wv[tid];
   PHASE_MARK(tph, "ref.rr");
-  cluster_barrier();
-  load_panel(sE, Qr, m * r);  // sE now holds Q_r
-  __syncthreads();
+  exchange_panel(sE, m, r, crank, rown);  // sE now holds Q_r
   // F4: Y = W^T Q_r Sigma^-2 (q x r) on own columns of W, staged kWChunk columns at a time
   const int blo = (q * crank) / NCL, bhi = (q * (crank + 1)) / NCL;
   for (int c0 = blo; c0 < bhi; c0 += kWChunk) {
@@ -1478,6 +1487,7 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
   }
   PHASE_MARK(tph, "ref.Y");
   TL_END(4 + 10 * mode);
+  cluster_barrier();  // no CTA leaves while another still reads its shared memory
 }
 
 }  // namespace

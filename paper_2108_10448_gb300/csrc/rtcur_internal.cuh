@@ -124,11 +124,9 @@ struct Bufs {
   double* gram;          // sum m_i^2
   float* jV;             // sum m_i^2, FP32 eigenvectors (m x m, row-major, column j = vector j)
   float* jL;             // sum m_i, FP32 eigenvalues
-  double* X1;            // sum m_i r_i, FP64 refined top-r basis
   double* Qr;            // sum m_i r_i, final orthonormal top-r basis
   double* sig;           // sum r_i, singular values (0 where truncated)
   double* Y;             // sum q_i r_i, V_r Sigma_r^-1
-  double* ework;         // 3 * sum m_i r_i + 3 * 16 * n, refinement scratch
   int* warm;             // n flags: the warm attempt produced mode i's factors this iteration
   double* wratio;        // n: ||C||_F / lambda_r of the last iteration (warm-attempt gate)
   double* Bpart;         // split-K partials of B (nchunk * sumB)
