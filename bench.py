@@ -667,7 +667,9 @@ def run_ours(a, rank, world):
     if rank != 0:
         return
     n_modes = 3
-    launches_per_iter = (1 if scope == rt.SCOPE_FULL else 0) + 1 + 1 + 1 + 1 + 2 + n_modes + 2 + 1 + 1
+    # per iteration: [dense pass] + threshold + Gram + warm refinement + eigensolver + refinement
+    # + B_i (partials, reduce) + one core stage per mode + table (2) + error + commit
+    launches_per_iter = (1 if scope == rt.SCOPE_FULL else 0) + 1 + 1 + 1 + 1 + 1 + 2 + n_modes + 2 + 1 + 1
     line = {
         "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": K,
         "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",

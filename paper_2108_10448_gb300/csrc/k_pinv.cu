@@ -843,8 +843,9 @@ __device__ __forceinline__ void exchange_panel(double* sP, int m, int r, int cra
 }
 
 // mode 1: full refinement after the FP32 eigensolver (skipped for a mode whose warm attempt
-//         succeeded). mode 0: warm attempt (RTCUR-F, k >= 1): three FP64 subspace-iteration
-//         steps from the previous iteration's basis, accepted only when certified (see below).
+//         succeeded). mode 0: warm attempt (k >= 1): three FP64 subspace-iteration steps (more
+//         while converging) from the previous iteration's basis (RTCUR-F) or from the current
+//         factor's rows on the new index set (RTCUR-R), accepted only when certified (see below).
 __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode) {
   TL_BEGIN();
   extern __shared__ double rsm[];
@@ -902,7 +903,7 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
   }
   if (mode == 0) {
     if (tid == 0 && crank == 0) *warm_flag = 0;
-    if (g.variant != 0 || b.st->k < 1) return;
+    if (b.st->k < 1) return;
     // skip the attempt when the last iteration's spectrum had no usable gap: its complement
     // block was at least kWarmGate times lambda_r, and the block moves slowly between iterations
     if (b.wratio[i] > kWarmGate) return;
@@ -937,10 +938,19 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
   __syncthreads();
   __shared__ int chol_ok;
   // One FP64 subspace-iteration step with a Cholesky QR: X1 <- (M X1) L^-T, L L^T = (M X1)^T (M X1).
+  // Each CTA forms its own rows of Y = M X1, the panel Y is exchanged, and every CTA then forms the
+  // whole new X1 = Y L^-T itself (the same data and order in every CTA, so the copies agree bit
+  // for bit): one cluster exchange per step. Y alternates between the panels sYw and sE, so a CTA
+  // writes a panel again only after the next step's barrier, by which every CTA has finished
+  // reading it; after a run of steps the caller passes one more cluster barrier before sYw or sE
+  // is written again.
   // False when the Cholesky fails, or when a pivot of L falls below min_pivot L_00 (a column of
   // M X1 with no resolvable part outside the others); the same data in every CTA of the cluster
   // gives a uniform outcome.
+  int sstep = 0;
   auto subspace_step = [&](double min_pivot) -> bool {
+    double* sYb = (sstep & 1) ? sE : sYw;
+    ++sstep;
     for (int t0 = tid >> 2; t0 < ((own * r + nq - 1) / nq) * nq; t0 += nq) {
       const int t = t0;
       const bool act = t < own * r;
@@ -951,13 +961,13 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
         for (int c = ql; c < m; c += 4) acc = fma(Ma[c], sX1[c * r + j], acc);
       }
       acc = quad_sum_d(acc);
-      if (act && ql == 0) sYw[(lo + a) * r + j] = acc;
+      if (act && ql == 0) sYb[(lo + a) * r + j] = acc;
     }
-    exchange_panel(sYw, m, r, crank, rown);
+    exchange_panel(sYb, m, r, crank, rown);
     for (int t = wid; t < r * r; t += nw) {
       int j = t / r, l = t % r;
       double acc = 0.0;
-      for (int a = lane; a < m; a += 32) acc = fma(sYw[a * r + j], sYw[a * r + l], acc);
+      for (int a = lane; a < m; a += 32) acc = fma(sYb[a * r + j], sYb[a * r + l], acc);
       acc = warp_sum_d(acc);
       if (lane == 0) Gq[t] = acc;
     }
@@ -969,35 +979,48 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
     }
     __syncthreads();
     if (!chol_ok) {
-      cluster_barrier();  // the other CTAs may still be reading this CTA's rows of sYw
+      cluster_barrier();  // the other CTAs may still be reading this CTA's rows of sYb
       return false;
     }
-    for (int a = lo + tid; a < hi; a += blockDim.x) {
+    for (int a = tid; a < m; a += blockDim.x) {
       double y[RT_MAXR];
 #pragma unroll
       for (int j = 0; j < RT_MAXR; ++j) {
         if (j < r) {
-          double v = sYw[a * r + j];
+          double v = sYb[a * r + j];
           for (int l = 0; l < j; ++l) v -= Gq[j * r + l] * y[l];
           y[j] = v * invd[j];
         }
       }
 #pragma unroll
       for (int j = 0; j < RT_MAXR; ++j)
-        if (j < r) sX1[a * r + j] = y[j];  // own rows only: no thread reads sX1 in this phase
+        if (j < r) sX1[a * r + j] = y[j];  // all rows: no thread reads sX1 in this phase
     }
-    exchange_panel(sX1, m, r, crank, rown);
+    __syncthreads();
     return true;
   };
   int oa_steps = g.refine_steps;  // Ogita-Aishima steps of the cold path
   if (mode == 0) {
-    // warm start: the previous iteration's top-r basis (complete in global memory), then FP64
-    // subspace iteration
-    load_panel(sX1, Qr, m * r);
+    // warm start, then FP64 subspace iteration. RTCUR-F keeps its index sets, so the previous
+    // iteration's top-r basis of W_i (complete in global memory) starts it. RTCUR-R draws new sets
+    // each iteration, so the start is the current iterate's factor restricted to the new rows,
+    // B_i(I_i, :) of L^(k): W_i = C_i(I_i, :) takes its columns from X - S, which L^(k) approximates,
+    // so its top-r left singular subspace is close to span B_i(I_i, :) (the first step
+    // orthonormalises it).
+    if (g.variant == 0) {
+      load_panel(sX1, Qr, m * r);
+    } else {
+      const float* Bk = b.B[b.st->k & 1] + g.offB[i];
+      for (int t = tid; t < m * r; t += blockDim.x) {
+        const int a = t / r, j = t - a * r;
+        sX1[t] = (double)Bk[set[g.ioff[i] + a] * r + j];
+      }
+    }
     __syncthreads();
   warm_steps:
     for (int it = 0; it < wsteps; ++it)
       if (!subspace_step(0.0)) return;  // not certified: the full path runs
+    cluster_barrier();  // every CTA has read the last step's panel
     wtotal += wsteps;
     oa_steps = 0;
   } else {
@@ -1019,7 +1042,10 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
       if (!subspace_step(1e-12)) break;
       ++done;
     }
-    if (done == kLowSteps) oa_steps = 0;
+    if (done == kLowSteps) {
+      cluster_barrier();  // every CTA has read the last step's panel
+      oa_steps = 0;
+    }
   }
   }
   PHASE_MARK(tph, "ref.init");
