@@ -777,6 +777,20 @@ constexpr float kLowLambda = 1e-4f;
 constexpr int kLowSteps = 4;
 constexpr double kWarmGate = 1.5;  // attempt only if ||C||_F / lambda_r was below this last time
 
+// 1 / sqrt(d) for d > 0 by Newton's iteration for the inverse square root,
+// y <- y + y (1 - d y^2) / 2, from an FP32 seed: the error e of y becomes ~1.5 e^2 per step, so
+// two steps take the seed's ~2^-22 to FP64 rounding level. Eight dependent FP64 operations,
+// against the two much longer sequences of a correctly rounded sqrt and a division; outside the
+// range where the FP32 seed is a normal number it falls back to those.
+__device__ __forceinline__ double rsqrt_newton(double d) {
+  if (!(d > 1e-35 && d < 1e35)) return 1.0 / sqrt(d);
+  double y = (double)rsqrtf((float)d);
+  double e = fma(-(d * y), y, 1.0);
+  y = fma(0.5 * y, e, y);
+  e = fma(-(d * y), y, 1.0);
+  return fma(0.5 * y, e, y);
+}
+
 // In-place Cholesky of the r x r SPD matrix G (row-major; the lower triangle is read and
 // overwritten with L, G = L L^T); inv[j] = 1 / L_jj so triangular solves multiply instead of
 // divide (FP64 division is a long dependent sequence on this part). Returns false when a pivot
@@ -786,8 +800,8 @@ __device__ bool chol_small(double* G, int r, double* inv) {
     double d = G[j * r + j];
     for (int l = 0; l < j; ++l) d -= G[j * r + l] * G[j * r + l];
     if (!(d > 0.0)) return false;
-    d = sqrt(d);
-    const double id = 1.0 / d;
+    const double id = rsqrt_newton(d);
+    d *= id;
     G[j * r + j] = d;
     inv[j] = id;
     for (int ii = j + 1; ii < r; ++ii) {
@@ -804,6 +818,15 @@ __host__ __device__ inline size_t refine_smem_bytes(int m, int r, int ncl) {
   return sizeof(double) * ((size_t)own * m + 3 * (size_t)m * r) +
          sizeof(float) * (2 * (size_t)own * m + (size_t)m * kWChunk);
 }
+
+// 4-byte asynchronous global -> shared copies (no register staging; the copies complete while
+// the thread runs on), committed as one group and awaited before the data is read
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ double warp_sum_d(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -869,7 +892,7 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
   __shared__ float lam[RT_MAXM];
   __shared__ unsigned char rown[RT_MAXM];  // cluster rank that owns each panel row
   for (int a = tid; a < m; a += blockDim.x) {
-    lam[a] = b.jL[g.offL[i] + a];
+    if (mode == 1) lam[a] = b.jL[g.offL[i] + a];  // the FP32 spectrum (not yet formed in mode 0)
     int c = (a * NCL) / m;
     while (c + 1 < NCL && (m * (c + 1)) / NCL <= a) ++c;
     while (c > 0 && (m * c) / NCL > a) --c;
@@ -908,8 +931,21 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
     // block was at least kWarmGate times lambda_r, and the block moves slowly between iterations
     if (b.wratio[i] > kWarmGate) return;
   }
-  if (tid == 0) {
-    tie = 0;
+  // the first chunk of W's columns for Y = W^T P, fetched while the refinement runs
+  const int blo = (q * crank) / NCL, bhi = (q * (crank + 1)) / NCL;
+  {
+    const int cn = min(kWChunk, bhi - blo);
+    const float* Wi = b.W + g.offW[i];
+    for (int t = tid; t < m * cn; t += blockDim.x) {
+      int cc = t / m, a = t - cc * m;
+      cp_async4(&sW[a * kWChunk + cc], Wi + (long long)a * q + blo + cc);
+    }
+    cp_async_commit();
+  }
+  if (tid == 0) tie = 0;
+  // the FP32 eigenbasis and its top-r columns: the cold path only (the warm attempt runs before
+  // the eigensolver of this iteration)
+  if (mode == 1 && tid == 0) {
     for (int a = 0; a < m; ++a) pos_of[a] = -1;
     for (int j = 0; j < r; ++j) {  // r largest eigenvalues, descending; ties broken by index
       int best = -1;
@@ -929,11 +965,16 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
   for (int t = tid; t < own * m; t += blockDim.x) {
     int a = t / m, c = t - a * m;
     sM[t] = M[(long long)(lo + a) * m + c];
-    sXr[t] = Xh[(long long)(lo + a) * m + c];
   }
-  for (int t = tid; t < m * own; t += blockDim.x) {
-    int a = t / own, j = t - a * own;
-    sXc[t] = Xh[(long long)a * m + lo + j];
+  if (mode == 1) {
+    for (int t = tid; t < own * m; t += blockDim.x) {
+      int a = t / m, c = t - a * m;
+      sXr[t] = Xh[(long long)(lo + a) * m + c];
+    }
+    for (int t = tid; t < m * own; t += blockDim.x) {
+      int a = t / own, j = t - a * own;
+      sXc[t] = Xh[(long long)a * m + lo + j];
+    }
   }
   __syncthreads();
   __shared__ int chol_ok;
@@ -1019,7 +1060,10 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
     __syncthreads();
   warm_steps:
     for (int it = 0; it < wsteps; ++it)
-      if (!subspace_step(0.0)) return;  // not certified: the full path runs
+      if (!subspace_step(0.0)) {  // not certified: the full path runs
+        cp_async_wait_all();
+        return;
+      }
     cluster_barrier();  // every CTA has read the last step's panel
     wtotal += wsteps;
     oa_steps = 0;
@@ -1202,50 +1246,72 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
       cslot[2] = a2;
     }
     cluster_barrier();
-    if (tid == 0) {
+    if (wid == 0) {  // the cluster's partials read in parallel, summed in rank order
+      double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+      if (lane < NCL) {
+        const double* slot = cl.map_shared_rank(cslot, (unsigned)lane);
+        v0 = slot[0];
+        v1 = slot[1];
+        v2 = slot[2];
+      }
       double a0 = 0.0, a1 = 0.0, a2 = 0.0;
       for (int c2 = 0; c2 < NCL; ++c2) {
-        const double* slot = cl.map_shared_rank(cslot, (unsigned)c2);
-        a0 += slot[0];
-        a1 += slot[1];
-        a2 += slot[2];
+        a0 += __shfl_sync(0xffffffffu, v0, c2);
+        a1 += __shfl_sync(0xffffffffu, v1, c2);
+        a2 += __shfl_sync(0xffffffffu, v2, c2);
       }
-      cert[0] = a0;
-      cert[1] = a1;
-      cert[2] = a2;
+      if (lane == 0) {
+        cert[0] = a0;
+        cert[1] = a1;
+        cert[2] = a2;
+      }
     }
     __syncthreads();
   }
-  if (tid == 0) {
-    // FP32 eigenvalues of H (cyclic Jacobi on an r x r copy) for the conditioning test
-    float hf[RT_MAXR * RT_MAXR];
-    for (int t = 0; t < r * r; ++t) {
+  // FP32 eigenvalues of H for the conditioning test: cyclic Jacobi on an r x r copy by warp 0
+  // (each rotation's row and column updates spread over the lanes, its angle computed by every
+  // lane from the same shared values); meanwhile thread 32 forms the FP64 Cholesky factor of H
+  // that the fast finish uses
+  __shared__ float hf[RT_MAXR * RT_MAXR];
+  __shared__ int hchol_ok;
+  if (wid == 0) {
+    for (int t = lane; t < r * r; t += 32) {
       int j = t / r, l = t % r;
       hf[t] = (float)(0.5 * (Hs[j * r + l] + Hs[l * r + j]));
     }
+    __syncwarp();
     for (int sw = 0; sw < 30; ++sw) {
       int nrot = 0;
       for (int p = 0; p < r - 1; ++p)
         for (int qq = p + 1; qq < r; ++qq) {
-          float apq = hf[p * r + qq], app = hf[p * r + p], aqq = hf[qq * r + qq];
+          const float apq = hf[p * r + qq], app = hf[p * r + p], aqq = hf[qq * r + qq];
           if (apq == 0.f || fabsf(apq) <= 1e-7f * sqrtf(fabsf(app * aqq))) continue;
           ++nrot;
-          float th = (aqq - app) / (2.f * apq);
-          float tt = (th >= 0.f ? 1.f : -1.f) / (fabsf(th) + sqrtf(th * th + 1.f));
-          float c = 1.f / sqrtf(tt * tt + 1.f), sn = tt * c;
-          for (int l = 0; l < r; ++l) {
-            float hp = hf[p * r + l], hq = hf[qq * r + l];
+          const float th = (aqq - app) / (2.f * apq);
+          const float tt = (th >= 0.f ? 1.f : -1.f) / (fabsf(th) + sqrtf(th * th + 1.f));
+          const float c = 1.f / sqrtf(tt * tt + 1.f), sn = tt * c;
+          __syncwarp();  // every lane has read the pivot entries
+          for (int l = lane; l < r; l += 32) {
+            const float hp = hf[p * r + l], hq = hf[qq * r + l];
             hf[p * r + l] = c * hp - sn * hq;
             hf[qq * r + l] = sn * hp + c * hq;
           }
-          for (int l = 0; l < r; ++l) {
-            float hp = hf[l * r + p], hq = hf[l * r + qq];
+          __syncwarp();
+          for (int l = lane; l < r; l += 32) {
+            const float hp = hf[l * r + p], hq = hf[l * r + qq];
             hf[l * r + p] = c * hp - sn * hq;
             hf[l * r + qq] = sn * hp + c * hq;
           }
+          __syncwarp();
         }
       if (nrot == 0) break;
     }
+  } else if (tid == 32) {
+    for (int t = 0; t < r * r; ++t) Gq[t] = 0.5 * (Hs[t] + Hs[(t % r) * r + t / r]);
+    hchol_ok = chol_small(Gq, r, invd) ? 1 : 0;
+  }
+  __syncthreads();
+  if (tid == 0) {
     float lmx = 0.f, lmn = 3.4e38f;
     for (int j = 0; j < r; ++j) { lmx = fmaxf(lmx, hf[j * r + j]); lmn = fminf(lmn, hf[j * r + j]); }
     fast_ok = (lmx > 0.f && lmn > 1e-6f * lmx) ? 1 : 0;
@@ -1272,9 +1338,8 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
       for (int j = 0; j < r; ++j)
         for (int l = j + 1; l < r; ++l)
           if (wv[l] > wv[j]) { double t = wv[j]; wv[j] = wv[l]; wv[l] = t; }
-      // FP64 Cholesky H = L L^T into Gq
-      for (int t = 0; t < r * r; ++t) Gq[t] = 0.5 * (Hs[t] + Hs[(t % r) * r + t / r]);
-      if (!chol_small(Gq, r, invd)) fast_ok = 0;
+      // FP64 Cholesky H = L L^T (in Gq, formed above)
+      if (!hchol_ok) fast_ok = 0;
     }
     if (tie && crank == 0) atomicOr(&b.st->flags, 2);
     else if (tie) atomicOr(&b.st->flags, 2);
@@ -1313,13 +1378,16 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
     }
     if (crank == 0 && tid < r) sig[tid] = wv[tid];
     exchange_panel(sE, m, r, crank, rown);  // sE holds P = X1 H^-1
-    // Y = W^T P (q x r) on own columns of W
-    const int blo = (q * crank) / NCL, bhi = (q * (crank + 1)) / NCL;
+    // Y = W^T P (q x r) on own columns of W (the first chunk was prefetched at entry)
     for (int c0 = blo; c0 < bhi; c0 += kWChunk) {
       const int cn = min(kWChunk, bhi - c0);
-      for (int t = tid; t < m * cn; t += blockDim.x) {
-        int cc = t / m, a = t - cc * m;
-        sW[a * kWChunk + cc] = w_entry(g, b, set, i, a, c0 + cc);
+      if (c0 == blo) {
+        cp_async_wait_all();
+      } else {
+        for (int t = tid; t < m * cn; t += blockDim.x) {
+          int cc = t / m, a = t - cc * m;
+          sW[a * kWChunk + cc] = w_entry(g, b, set, i, a, c0 + cc);
+        }
       }
       __syncthreads();
       for (int t0 = tid >> 2; t0 < ((cn * r + nq - 1) / nq) * nq; t0 += nq) {
@@ -1344,6 +1412,7 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
     return;
   }
   if (mode == 0) {  // not certified: the eigensolver and the full refinement run
+    cp_async_wait_all();
     cluster_barrier();  // no CTA leaves while another still reads its shared memory
     return;
   }
@@ -1491,13 +1560,17 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
   if (crank == 0 && tid < r) sig[tid] = wv[tid];
   PHASE_MARK(tph, "ref.rr");
   exchange_panel(sE, m, r, crank, rown);  // sE now holds Q_r
-  // F4: Y = W^T Q_r Sigma^-2 (q x r) on own columns of W, staged kWChunk columns at a time
-  const int blo = (q * crank) / NCL, bhi = (q * (crank + 1)) / NCL;
+  // F4: Y = W^T Q_r Sigma^-2 (q x r) on own columns of W, staged kWChunk columns at a time (the
+  // first chunk was prefetched at entry)
   for (int c0 = blo; c0 < bhi; c0 += kWChunk) {
     const int cn = min(kWChunk, bhi - c0);
-    for (int t = tid; t < m * cn; t += blockDim.x) {
-      int cc = t / m, a = t - cc * m;
-      sW[a * kWChunk + cc] = w_entry(g, b, set, i, a, c0 + cc);
+    if (c0 == blo) {
+      cp_async_wait_all();
+    } else {
+      for (int t = tid; t < m * cn; t += blockDim.x) {
+        int cc = t / m, a = t - cc * m;
+        sW[a * kWChunk + cc] = w_entry(g, b, set, i, a, c0 + cc);
+      }
     }
     __syncthreads();
     for (int t = wid; t < cn * r; t += nw) {
