@@ -17,9 +17,11 @@
 //     B_n is the A operand, staged once per launch, one 128-row block per column block;
 //   * two epilogue warpgroups, warpgroup h on rows 8h..8h+7 of every tile: tcgen05.ld of its 8
 //     accumulator columns per block (warp w reads TMEM lanes 32(w%4)..: 32 columns of X), X from
-//     its half stage, threshold, S written in place; the half tile leaves in one 1-D bulk store and
-//     its stage is refilled once that store has read it (checked at the warpgroup's next store). The
-//     residual / nnz / band sums are fused.
+//     its half stage, threshold, S written in place, then an arrive on the stage's done barrier
+//     (each warp on its own: no barrier inside the warpgroup). The residual / nnz / band sums are
+//     fused;
+//   * store warp: once the four warps of a half tile have arrived, one 1-D bulk store of it; a
+//     stage goes back to the producer once its store has read it (checked at the next store).
 // Forms (FP32 accumulation in both):
 //   BF16: kind::f16 with BF16 operands split x = hi + lo, the three significant products
 //         B_hi T_hi + B_hi T_lo + B_lo T_hi packed along K = 16 (3 r_n <= 15); the dropped lo*lo
@@ -34,7 +36,8 @@
 namespace {
 
 constexpr int kUEpiWarps = 8;                      // warps 0-7: epilogue (two warpgroups)
-constexpr int kUThreads = 32 * (kUEpiWarps + 2);   // + warp 8: bulk-copy producer, warp 9: MMA
+// + warp 8: bulk-copy producer, warp 9: MMA, warp 10: bulk stores of S
+constexpr int kUThreads = 32 * (kUEpiWarps + 3);
 constexpr int kURows = 16;                         // rows per tile (N of the MMA)
 constexpr int kUHalf = kURows / 2;                 // rows per ring stage (one warpgroup's half)
 constexpr int kUCols = 128;                        // columns per block (M of the MMA)
@@ -42,13 +45,13 @@ constexpr int kUMaxStages = 8;
 constexpr int kUOpBytesA = kUCols * 32;            // A: 128 rows (columns of X) x 32 bytes of K
 constexpr int kUOpBytesB = kURows * 32;            // B: 16 rows of T x 32 bytes of K
 constexpr int kUMaxCb = 8;                         // column blocks (d_n <= 1024)
-constexpr int kUGroup = 4;                         // blocks read from TMEM per wait
+constexpr int kUGroup = 2;                         // blocks read from TMEM per wait
 constexpr int kUTmemCols = 2 * kUMaxCb * kURows;   // two tiles of up to 8 blocks x 16 columns
 constexpr long long kUSpin = 1LL << 26;
 constexpr int kUMaxRed = 1024;
 // Room left on the SM for one CTA of the sampled chain's cluster kernel (256 threads x 128
 // registers, ~40 KB of shared memory), which runs beside this pass: registers are split among the
-// SM's four schedulers, three of this kernel's ten warps share one, so 80 registers a thread.
+// SM's four schedulers, three of this kernel's eleven warps share one, so 80 registers a thread.
 constexpr int kUMaxRegs = 80;
 constexpr int kUSmemLimit = 184 * 1024;            // dynamic shared memory of this pass
 
@@ -69,25 +72,6 @@ __device__ __forceinline__ bool mb_wait(unsigned bar, unsigned parity) {
     if (mb_try(bar, parity)) return true;
   return false;
 }
-// Named barriers of one epilogue warpgroup (128 threads). The id is an immediate: a barrier id in
-// a register makes the compiler reserve all 16 hardware barriers of the CTA, which keeps other
-// kernels' CTAs (the sampled chain's) off the SM.
-template <int ID>
-__device__ __forceinline__ bool wg_and(bool v) {
-  unsigned out;
-  asm volatile(
-      "{\n\t.reg .pred pi, po;\n\tsetp.ne.u32 pi, %1, 0;\n\tbar.red.and.pred po, %2, 128, pi;\n\t"
-      "selp.u32 %0, 1, 0, po;\n\t}"
-      : "=r"(out)
-      : "r"(v ? 1u : 0u), "n"(ID)
-      : "memory");
-  return out != 0;
-}
-template <int ID>
-__device__ __forceinline__ void wg_sync() {
-  asm volatile("bar.sync %0, 128;" ::"n"(ID) : "memory");
-}
-
 // K-major, no-swizzle operand block: row m (0..127), byte b (0..31) of its K slice.
 __device__ __forceinline__ unsigned op_off(int m, int b) {
   return (unsigned)((m >> 3) * 256 + (b >> 4) * 128 + (m & 7) * 16 + (b & 15));
@@ -155,15 +139,19 @@ __device__ __forceinline__ void op_row(const float* v, int r, bool a_side, unsig
 
 // One element of the epilogue: D = X - L in place of X (the stage), kept when |D| > zeta, with
 // the residual, kept-count and band-count sums.
-__device__ __forceinline__ void ht1(float* p, unsigned lbits, float zf, float band, float& res, unsigned& nnz,
-                                    unsigned& inb) {
-  const float dl = *p - __uint_as_float(lbits);
+__device__ __forceinline__ float ht1v(float x, unsigned lbits, float zf, float band, float& res, unsigned& nnz,
+                                     unsigned& inb) {
+  const float dl = x - __uint_as_float(lbits);
   const float ad = fabsf(dl);
   const bool keep = ad > zf;
-  *p = keep ? dl : 0.f;
   res = keep ? res : fmaf(dl, dl, res);
   nnz += keep ? 1u : 0u;
   inb += (fabsf(ad - zf) <= band) ? 1u : 0u;
+  return keep ? dl : 0.f;
+}
+__device__ __forceinline__ void ht1(float* p, unsigned lbits, float zf, float band, float& res, unsigned& nnz,
+                                    unsigned& inb) {
+  *p = ht1v(*p, lbits, zf, band, res, nnz, inb);
 }
 // A warp is done reading a TMEM accumulator: order its loads before the arrive on `bar`.
 __device__ __forceinline__ void release_acc(unsigned long long* bar, int lane) {
@@ -184,6 +172,25 @@ __device__ __forceinline__ void tmem_group(unsigned tq, int cb0, int nq, unsigne
                    : "r"(tq + (unsigned)((cb0 + c) * kURows)));
 }
 
+// The repeated last block (index cb): its 8 accumulator columns of this warp are loaded as for a
+// full block (completed by tcgen05.wait::ld); tail_pick then keeps the rows of the half tile
+// that lane quarter tk's copy handles, 2 tk, 2 tk + 1 (4 copies) or 4 tk .. 4 tk + 3 (2 copies).
+__device__ __forceinline__ void tail_load8(unsigned tq, int cb, unsigned (&w)[kUHalf]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7])
+               : "r"(tq + (unsigned)(cb * kURows)));
+}
+__device__ __forceinline__ void tail_pick(const unsigned (&w)[kUHalf], int trep, int tk, unsigned (&v)[4]) {
+  if (trep == 4) {
+    v[0] = tk == 0 ? w[0] : (tk == 1 ? w[2] : (tk == 2 ? w[4] : w[6]));
+    v[1] = tk == 0 ? w[1] : (tk == 1 ? w[3] : (tk == 2 ? w[5] : w[7]));
+    v[2] = v[3] = 0u;
+  } else {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] = tk == 0 ? w[e] : w[4 + e];
+  }
+}
+
 __device__ __forceinline__ double block_sum_u(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -199,9 +206,9 @@ __device__ __forceinline__ double block_sum_u(double v, double* sh) {
 template <int KIND>
 __global__ void __maxnreg__(kUMaxRegs) k_dense_umma(Geom g, Bufs b, int nstages) {
   extern __shared__ __align__(128) unsigned char dsm[];
-  __shared__ unsigned long long xfull[kUMaxStages], xempty[kUMaxStages], tfull[2], tempty[2];
+  __shared__ unsigned long long xfull[kUMaxStages], xempty[kUMaxStages], sdone[kUMaxStages], tfull[2], tempty[2];
   __shared__ unsigned tbase;
-  __shared__ volatile int ep_abort, prod_abort, mma_abort;  // set to 1 only
+  __shared__ volatile int ep_abort, prod_abort, mma_abort, st_abort;  // set to 1 only
   __shared__ int n_issued[kUMaxStages], n_mma[2];
   __shared__ double sh[kUThreads / 32];
   TL_BEGIN();
@@ -226,10 +233,19 @@ __global__ void __maxnreg__(kUMaxRegs) k_dense_umma(Geom g, Bufs b, int nstages)
   const long long u0 = ntiles * blockIdx.x / gridDim.x, u1 = ntiles * (blockIdx.x + 1) / gridDim.x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  // A operand: row m of column block cb is B_n(cb * 128 + m, :) (zero beyond d_n)
+  // Last column block: its w = d_n - 128 (ncb - 1) columns are repeated trep = 4 (w <= 32) or
+  // 2 (w <= 64) times down the 128 TMEM lanes, so every lane quarter holds a copy and the four
+  // quarters' warps split its rows (trep = 1: one copy, as the other blocks). Without the copies
+  // the warps of lane quarter 0 alone would hold a narrow last block (at d_n = 800, 7 blocks
+  // against 6 for the others).
+  const int wtail = dn - (ncb - 1) * kUCols;
+  const int trep = wtail <= 32 ? 4 : (wtail <= 64 ? 2 : 1);
+  const int tspan = kUCols / trep;  // lanes per copy
+  // A operand: row m of column block cb is B_n(cb * 128 + m, :), of the last block
+  // B_n(cb * 128 + m mod tspan, :) (zero beyond d_n)
   for (int e = tid; e < ncb * kUCols; e += kUThreads) {
     const int cb = e / kUCols, m = e % kUCols;
-    const int col = cb * kUCols + m;
+    const int col = cb * kUCols + (cb == ncb - 1 ? m % tspan : m);
     float v[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) v[c] = (col < dn && c < rn) ? __ldg(Bn + (size_t)col * rn + c) : 0.f;
@@ -240,11 +256,12 @@ __global__ void __maxnreg__(kUMaxRegs) k_dense_umma(Geom g, Bufs b, int nstages)
     *reinterpret_cast<uint4*>(blk + op_off(m, 16)) = make_uint4(w[4], w[5], w[6], w[7]);
   }
   if (tid == 0) {
-    ep_abort = prod_abort = mma_abort = 0;
+    ep_abort = prod_abort = mma_abort = st_abort = 0;
     for (int s = 0; s < kUMaxStages; ++s) {
       n_issued[s] = 0;
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&xfull[s])) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&xempty[s])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&sdone[s])), "r"(kUEpiWarps / 2) : "memory");
     }
     for (int a = 0; a < 2; ++a) {
       n_mma[a] = 0;
@@ -274,7 +291,7 @@ __global__ void __maxnreg__(kUMaxRegs) k_dense_umma(Geom g, Bufs b, int nstages)
       const long long nj = 2 * (u1 - u0);
       for (long long j = 0; j < nj; ++j) {
         const int s = (int)(j % nstages);
-        if (ep_abort || mma_abort) break;
+        if (ep_abort || mma_abort || st_abort) break;
         if (j >= nstages && !mb_wait(su32(&xempty[s]), (unsigned)(((j / nstages) - 1) & 1))) {
           prod_abort = 1;
           break;
@@ -349,12 +366,41 @@ __global__ void __maxnreg__(kUMaxRegs) k_dense_umma(Geom g, Bufs b, int nstages)
       }
       __syncwarp();
     }
+  } else if (warp == kUEpiWarps + 2) {
+    // ---------------- store warp: half tiles in order, each once its four epilogue warps are done
+    if (lane == 0) {
+      const long long nj = 2 * (u1 - u0);
+      for (long long j = 0; j < nj; ++j) {
+        const int s = (int)(j % nstages);
+        if (!mb_wait(su32(&sdone[s]), (unsigned)((j / nstages) & 1))) {
+          st_abort = 1;
+          break;
+        }
+        const long long r0 = (u0 + (j >> 1)) * kURows + (j & 1) * kUHalf;
+        const long long nr = r0 >= rows ? 0 : (r0 + kUHalf <= rows ? kUHalf : rows - r0);
+        if (nr > 0)
+          asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(S + r0 * dn),
+                       "r"(su32(ring + (size_t)s * stage_f)), "r"((unsigned)(nr * dn * 4))
+                       : "memory");
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        if (j >= 1) {  // the previous half tile's store has read its stage: release it
+          asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&xempty[(j - 1) % nstages]))
+                       : "memory");
+        }
+      }
+      asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // S is in memory
+    }
   } else {
     // ---------------- epilogue: warpgroup h on rows 8h..8h+7 of each tile (its half stage)
     const int q = warp & 3;  // TMEM lane quarter: columns 32q.. of every block
     const int h = warp >> 2;
-    const int et = tid & 127;
-    const int nq = (dn - q * 32 + kUCols - 1) / kUCols;  // blocks with columns in this quarter
+    // blocks handled in the group loop: those with columns in this quarter, less the repeated
+    // last block
+    const int nfull = trep > 1 ? ncb - 1 : (dn - q * 32 + kUCols - 1) / kUCols;
+    // in the repeated last block: this lane's column and the rows (of the half tile) of its copy
+    const int tcol = (ncb - 1) * kUCols + ((q * 32 + lane) % tspan);
+    const int tk = (q * 32) / tspan;
     for (long long u = u0; u < u1; ++u) {
       const int i = (int)(u - u0), a = i & 1;
       const long long j = 2 * (long long)i + h;
@@ -363,37 +409,54 @@ __global__ void __maxnreg__(kUMaxRegs) k_dense_umma(Geom g, Bufs b, int nstages)
       const int nr = (int)(r0 >= rows ? 0 : (r0 + kUHalf <= rows ? kUHalf : rows - r0));
       const bool ok_t = mb_wait(su32(&tfull[a]), (unsigned)((i >> 1) & 1));
       const bool ok_x = ok_t && mb_wait(su32(&xfull[s]), (unsigned)((j / nstages) & 1));
-      // AND over the warpgroup: its threads leave together
-      const bool allok = h == 0 ? wg_and<1>(ok_t && ok_x) : wg_and<2>(ok_t && ok_x);
-      if (!allok) {
-        if (et == 0) ep_abort = 1;
+      if (!__all_sync(0xffffffffu, ok_t && ok_x)) {  // the warp leaves together
+        if (lane == 0) ep_abort = 1;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       // this warp's 8 accumulator columns of each block, kUGroup blocks per wait; the accumulator
-      // goes back to the MMA warp after the last group's loads
+      // goes back to the MMA warp after the last loads. The repeated last block is loaded and
+      // handled after the loop, so its code exists once.
       const unsigned tq = tmem + ((unsigned)(q * 32) << 16) + (unsigned)(a * (kUTmemCols / 2) + h * kUHalf);
       float* stg = ring + (size_t)s * stage_f;
       bool freed = false;
 #pragma unroll
       for (int g0 = 0; g0 < kUMaxCb; g0 += kUGroup) {
-        if (g0 >= nq) break;  // warp-uniform
+        if (g0 >= nfull) break;  // warp-uniform
         unsigned l[kUGroup][kUHalf];
-        tmem_group(tq, g0, nq, l);
+        tmem_group(tq, g0, nfull, l);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (g0 + kUGroup >= nq) {
+        if (trep == 1 && g0 + kUGroup >= nfull) {
           release_acc(&tempty[a], lane);
           freed = true;
         }
+        if (nr == kUHalf) {
+          // the group's X values first, then S: written this way the loads are not ordered after
+          // the stores (whose addresses, a runtime stride apart, the compiler cannot tell apart)
+          float xv[kUGroup][kUHalf];
 #pragma unroll
-        for (int c = 0; c < kUGroup; ++c) {
-          const int col = (g0 + c) * kUCols + q * 32 + lane;
-          if (g0 + c < nq && col < dn) {
-            float* p = stg + col;
-            if (nr == kUHalf) {
+          for (int c = 0; c < kUGroup; ++c) {
+            const int col = (g0 + c) * kUCols + q * 32 + lane;
+            if (g0 + c < nfull && col < dn) {
 #pragma unroll
-              for (int r = 0; r < kUHalf; ++r) ht1(p + r * dn, l[c][r], zf, band, res, nnz, inb);
-            } else {
+              for (int r = 0; r < kUHalf; ++r) xv[c][r] = stg[col + r * dn];
+            }
+          }
+#pragma unroll
+          for (int c = 0; c < kUGroup; ++c) {
+            const int col = (g0 + c) * kUCols + q * 32 + lane;
+            if (g0 + c < nfull && col < dn) {
+#pragma unroll
+              for (int r = 0; r < kUHalf; ++r)
+                stg[col + r * dn] = ht1v(xv[c][r], l[c][r], zf, band, res, nnz, inb);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < kUGroup; ++c) {
+            const int col = (g0 + c) * kUCols + q * 32 + lane;
+            if (g0 + c < nfull && col < dn) {
+              float* p = stg + col;
 #pragma unroll
               for (int r = 0; r < kUHalf; ++r)
                 if (r < nr) ht1(p + r * dn, l[c][r], zf, band, res, nnz, inb);
@@ -401,27 +464,33 @@ __global__ void __maxnreg__(kUMaxRegs) k_dense_umma(Geom g, Bufs b, int nstages)
           }
         }
       }
-      if (!freed) release_acc(&tempty[a], lane);  // no column of this quarter
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // S half tile -> bulk store
-      if (h == 0) wg_sync<1>();
-      else wg_sync<2>();
-      if (et == 0) {
-        if (nr > 0)
-          asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(S + r0 * dn),
-                       "r"(su32(stg)), "r"((unsigned)(nr * dn * 4))
-                       : "memory");
-        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-        if (i >= 1) {  // this warpgroup's previous store has read its stage: release it
-          asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
-          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&xempty[(j - 2) % nstages]))
-                       : "memory");
+      if (trep > 1) {
+        unsigned tw[kUHalf], tv[4];  // the repeated last block: loaded, and this quarter's rows
+        tail_load8(tq, ncb - 1, tw);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        tail_pick(tw, trep, tk, tv);
+        release_acc(&tempty[a], lane);
+        freed = true;
+        if (tcol < dn) {
+          float* p = stg + tcol;
+          const int rb = (trep == 4 ? 2 : 4) * tk, cnt = trep == 4 ? 2 : 4;
+          float xt[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (e < cnt && rb + e < nr) xt[e] = p[(rb + e) * dn];
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (e < cnt && rb + e < nr) p[(rb + e) * dn] = ht1v(xt[e], tv[e], zf, band, res, nnz, inb);
         }
       }
+      if (!freed) release_acc(&tempty[a], lane);  // no column of this quarter
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // S half tile -> bulk store
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&sdone[s])) : "memory");
     }
-    if (et == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // S is in memory
   }
   __syncthreads();
-  if ((ep_abort || prod_abort || mma_abort) && tid == 0) {
+  if ((ep_abort || prod_abort || mma_abort || st_abort) && tid == 0) {
     // drain: every bulk load and MMA this CTA issued completes before its shared and tensor
     // memory are released (at most one outstanding per stage and per accumulator; waiting on a
     // completed phase returns at once)
@@ -473,7 +542,9 @@ int umma_stages(const Geom& g, int kind) {
   const long long stage = (long long)kUHalf * dn * 4;
   long long n = (kUSmemLimit - fixed) / stage;
   if (n > kUMaxStages) n = kUMaxStages;
-  return n >= 3 ? (int)n : 0;  // three stages at least: a stage is released one half tile late
+  // four stages at least: with three, one warpgroup can reach a stage whose previous load (a half
+  // tile of the other warpgroup) has not completed, and the parity wait on it would pass early
+  return n >= 4 ? (int)n : 0;
 }
 
 }  // namespace
@@ -501,7 +572,7 @@ cudaError_t launch_umma(const Geom& g, const Bufs& b, int kind, cudaStream_t s) 
   if (!smem) return cudaErrorNotSupported;
   const int ns = umma_stages(g, kind);
   const long long ntiles = (g.rowsT + kURows - 1) / kURows;
-  const int ctas = g.dense_ctas > 0 ? g.dense_ctas : 144;
+  const int ctas = g.dense_ctas > 0 ? g.dense_ctas : 148;
   const int grid = (int)(ntiles < ctas ? ntiles : ctas);
   if (kind == 0)
     k_dense_umma<0><<<grid, kUThreads, smem, s>>>(g, b, ns);
