@@ -249,8 +249,10 @@ __device__ __forceinline__ void emit_row(unsigned* mrow, float* vblk, float4 sv,
 //         b of word w of row r is S(r, 32 w + b) != 0) and, for each 128-column block of a row,
 //         its nonzero values in order from the block's first element index on. At 30% density
 //         that is 4 + 1/8 + 1.2 bytes per element instead of 8.
-template <int RN, int MODE>
-__global__ void __launch_bounds__(1024, 1) k_dense_tma(Geom g, Bufs b, int tr, int copy_sel, float* out) {
+// PAIR (MODE 0 only, blocks of at most 512 threads, i.e. d_n <= 2048): the row loop takes two
+// rows per step, which needs more than the 64 registers a thread that a 1024-thread block allows.
+template <int RN, int MODE, bool PAIR = false>
+__global__ void __launch_bounds__(PAIR ? 512 : 1024, 1) k_dense_tma(Geom g, Bufs b, int tr, int copy_sel, float* out) {
   TL_BEGIN();
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ unsigned long long full[kStages];
@@ -400,6 +402,54 @@ __global__ void __launch_bounds__(1024, 1) k_dense_tma(Geom g, Bufs b, int tr, i
       const bool act = c4 < n4;
       const float4* tile = ring + (size_t)s * stage_f4;
       const float* ttile = tring + (size_t)s * tstage + (r0 * RN - ((r0 * RN) & ~3LL));
+      if (PAIR) {
+        // two rows per step: both rows' T and X values are read before either S row is written
+        // (row by row, each read waits for the previous row's store, whose address lies a runtime
+        // stride away and so cannot be told apart by the compiler)
+        for (int rr = grp; rr < nr && act; rr += 2 * G) {
+          const int rb = rr + G;
+          const bool two = rb < nr;
+          float ta[RN], tb[RN];
+#pragma unroll
+          for (int c = 0; c < RN; ++c) {
+            ta[c] = ttile[rr * RN + c];
+            tb[c] = two ? ttile[rb * RN + c] : 0.f;
+          }
+          float4 xa = make_float4(0.f, 0.f, 0.f, 0.f), xb = xa;
+          if (MODE != 1) {
+            xa = tile[rr * n4 + c4];
+            if (two) xb = tile[rb * n4 + c4];
+          }
+          float La[4] = {0.f, 0.f, 0.f, 0.f}, Lb[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+          for (int c = 0; c < RN; ++c)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              La[j] = fmaf(ta[c], br[j][c], La[j]);
+              Lb[j] = fmaf(tb[c], br[j][c], Lb[j]);
+            }
+          float4 sa, sb;
+          if (MODE == 1) {
+            sa = make_float4(La[0], La[1], La[2], La[3]);
+            sb = make_float4(Lb[0], Lb[1], Lb[2], Lb[3]);
+          } else {
+            sa = sb = make_float4(0.f, 0.f, 0.f, 0.f);
+            ht_acc(xa.x, La[0], zf, band, sa.x, res, nnz, inb);
+            ht_acc(xa.y, La[1], zf, band, sa.y, res, nnz, inb);
+            ht_acc(xa.z, La[2], zf, band, sa.z, res, nnz, inb);
+            ht_acc(xa.w, La[3], zf, band, sa.w, res, nnz, inb);
+            if (two) {
+              ht_acc(xb.x, Lb[0], zf, band, sb.x, res, nnz, inb);
+              ht_acc(xb.y, Lb[1], zf, band, sb.y, res, nnz, inb);
+              ht_acc(xb.z, Lb[2], zf, band, sb.z, res, nnz, inb);
+              ht_acc(xb.w, Lb[3], zf, band, sb.w, res, nnz, inb);
+            }
+            if (zero_out) sa = sb = make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+          const_cast<float4*>(tile)[rr * n4 + c4] = sa;  // in place: one copy out
+          if (two) const_cast<float4*>(tile)[rb * n4 + c4] = sb;
+        }
+      } else
       for (int rr = grp; rr < nr; rr += G) {
         float4 sv = make_float4(0.f, 0.f, 0.f, 0.f);
         if (act) {
@@ -507,7 +557,9 @@ __global__ void __launch_bounds__(1024, 1) k_dense_tma(Geom g, Bufs b, int tr, i
 template <int RN>
 cudaError_t launch_tma_rn(const Geom& g, const Bufs& b, int tr, size_t smem, int grid, int threads,
                           cudaStream_t s, int mode = 0, int copy_sel = 0, float* out = nullptr) {
-  if (mode == 0)
+  if (mode == 0 && threads <= 512)
+    k_dense_tma<RN, 0, true><<<grid, threads, smem, s>>>(g, b, tr, copy_sel, out);
+  else if (mode == 0)
     k_dense_tma<RN, 0><<<grid, threads, smem, s>>>(g, b, tr, copy_sel, out);
   else if (mode == 3)
     k_dense_tma<RN, 3><<<grid, threads, smem, s>>>(g, b, tr, copy_sel, out);
@@ -524,8 +576,8 @@ cudaError_t launch_tma_rn(const Geom& g, const Bufs& b, int tr, size_t smem, int
 template <int RN>
 cudaError_t prepare_tma_rn(size_t smem) {
   cudaError_t e = cudaSuccess;
-  void* fns[4] = {(void*)k_dense_tma<RN, 0>, (void*)k_dense_tma<RN, 1>, (void*)k_dense_tma<RN, 2>,
-                  (void*)k_dense_tma<RN, 3>};
+  void* fns[5] = {(void*)k_dense_tma<RN, 0>, (void*)k_dense_tma<RN, 1>, (void*)k_dense_tma<RN, 2>,
+                  (void*)k_dense_tma<RN, 3>, (void*)k_dense_tma<RN, 0, true>};
   for (void* f : fns) {
     if (e == cudaSuccess) e = raise_smem_limit((const void*)f, (size_t)(smem));
     if (e == cudaSuccess)
