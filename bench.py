@@ -32,13 +32,13 @@ METRIC = "RTCUR iters/s & time-to-1e-5 at 800³ rank 5: BF16/TF32 vs FP32 plain,
 
 NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e nominal bandwidth (context for the roofline fraction)
 
-# DRAM bytes (read + write) of one launch of the FP32 fused dense pass k_dense_tma<5,0>, from an
+# DRAM bytes (read + write) of one launch of the FP32 fused dense pass k_dense_tma<5,0,1>, from an
 # ncu capture of two back-to-back launches at 600^3 without cache control (the second launch: the
 # dirty lines the first left in L2 are written back inside it, as its own are after it), scaled
 # by the element count. None until that capture exists; must be dropped whenever the kernel
 # changes.
-DENSE_TRAFFIC_PER_ELEMENT = 1734182400.0 / 216e6  # 8.029 B per element
-DENSE_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_dense_tma<5,0>, 600^3, "
+DENSE_TRAFFIC_PER_ELEMENT = 1734200064.0 / 216e6  # 8.029 B per element
+DENSE_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_dense_tma<5,0,1>, 600^3, "
                         "second of two back-to-back launches, --cache-control none, scaled by elements "
                         "(profiles/k_dense_tma_traffic_600.md)")
 
@@ -523,7 +523,7 @@ def run_ours(a, rank, world):
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "traffic_source": DENSE_TRAFFIC_SOURCE if traffic is not None else None,
-                "kernel": f"k_dense_tma<{p.ranks[-1]},0>", "ms_per_launch": dms,
+                "kernel": f"k_dense_tma<{p.ranks[-1]},0,{int(p.dims[-1] <= 2048)}>", "ms_per_launch": dms,
                 "peak_source": f"{src} (burst copy bandwidth); the >= 0.70 target is judged on it",
                 "frac_of_nominal": achieved / NOMINAL_HBM_GBS, "nominal_peak": NOMINAL_HBM_GBS,
                 "iteration_frac": alg_bytes / (ms / K / 1e3) / 1e9 / peak,
