@@ -650,18 +650,29 @@ def run_ours(a, rank, world):
             rt.rtcur_destroy(bp)
             sampled_ttt[v]["sample_x_bf16"] = {"ms": b_ms, "iters": bres.iters, "e": bres.e,
                                                "note": "includes the BF16 copy of X made by rtcur_begin"}
-    # --- end to end through the C ABI from pinned host buffers ---
+    # --- end to end through the C ABI from pinned host buffers: H2D X, the solve, and the
+    # download of Algorithm 1's output (R, C_i, U_i^+, from which L = R x_i (C_i U_i^+)); beside
+    # it the same solve with the dense L^(K) downloaded instead (the host link, ~0.2 TB/s each way,
+    # then takes as long as the solve)
     Xh = torch.from_numpy(p.X).pin_memory()
     Lh = torch.empty_like(Xh).pin_memory()
     Xd = torch.empty_like(X)
     t0 = time.perf_counter()
     with torch.cuda.stream(stream):
         Xd.copy_(Xh, non_blocking=True)
-        res_e2e = rt.rtcur_solve(plan, Xd.data_ptr(), idx, L.data_ptr(), 0, sh, max_iter=max_iter)
-        Lh.copy_(L, non_blocking=True)
+        res_e2e = rt.rtcur_solve(plan, Xd.data_ptr(), idx, 0, 0, sh, max_iter=max_iter)
+        cur = rt.rtcur_get_cur(plan, p.dims, p.m, p.q, sh)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e_val = world * res_e2e.iters / e2e_s
+    cur_bytes = int(cur[0].nbytes + sum(c.nbytes for c in cur[1]) + sum(u.nbytes for u in cur[2]))
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        Xd.copy_(Xh, non_blocking=True)
+        res_l = rt.rtcur_solve(plan, Xd.data_ptr(), idx, L.data_ptr(), 0, sh, max_iter=max_iter)
+        Lh.copy_(L, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_l_s = time.perf_counter() - t0
     rt.rtcur_destroy(plan)
     del Xd, Xh, Lh
     if rank != 0:
@@ -680,8 +691,12 @@ def run_ours(a, rank, world):
                         "warm_hits": res.warm_hits, "statistic": "median of 5 solves after 2 warm-up solves",
                         "includes": "index upload, max|X|, the graph-driven loop, L and S output"},
         "e2e": {"value": e2e_val, "unit": "iters/s", "seconds": e2e_s, "iters": res_e2e.iters,
-                "h2d_bytes_per_step": int(p.X.nbytes), "d2h_bytes_per_step": int(p.X.nbytes),
-                "step": "one whole solve: H2D X, rtcur_solve to 1e-5, D2H L"},
+                "h2d_bytes_per_step": int(p.X.nbytes) + int(idx.nbytes), "d2h_bytes_per_step": cur_bytes,
+                "step": "one whole solve: H2D X (and the index sets), rtcur_solve to 1e-5, D2H of "
+                        "Algorithm 1's output R, C_i, U_i^+ (rtcur_get_cur)",
+                "dense_L": {"value": world * res_l.iters / e2e_l_s, "seconds": e2e_l_s,
+                            "d2h_bytes_per_step": int(p.X.nbytes),
+                            "step": "the same with the dense L (prod d_i floats) downloaded instead"}},
         "roofline": roof,
         "other_variant": var_out,
         "sampled_time_to_tol": sampled_ttt or None,
