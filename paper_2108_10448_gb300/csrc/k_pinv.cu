@@ -448,10 +448,10 @@ __global__ void __launch_bounds__(kJacThreads, 1) k_eig_tri(Geom g, Bufs b) {
     TL_END(16);
     return;
   }
-  __shared__ float dv[kTriMax], ev[kTriMax], e2[kTriMax], tauv[kTriMax], vb[kTriMax], pv[kTriMax];
+  __shared__ float dv[kTriMax], ev[kTriMax], e2[kTriMax], tauv[kTriMax], pv[kTriMax];
   __shared__ float lam[kTriMax], qt[kTriMax];
   __shared__ int cid[kTriMax], inbig[kTriMax], known[kTriMax];
-  __shared__ float sh_scale, sh_tau, sh_lo, sh_hi, sh_nrm, sh_pivmin;
+  __shared__ float sh_lo, sh_hi, sh_nrm, sh_pivmin;
   __shared__ int sh_big, sh_nknown;
   const int i = blockIdx.x;
   const int m = g.m[i];
@@ -465,46 +465,38 @@ __global__ void __launch_bounds__(kJacThreads, 1) k_eig_tri(Geom g, Bufs b) {
     for (int c = lane; c < m; c += 32) A[r * kTriLd + c] = (float)M64[(long long)r * m + c];
   __syncthreads();
   PHASE_MARK(tph, "tri.load");
-  // ---- a. tridiagonalisation
+  // ---- a. tridiagonalisation. Two block barriers a step: every warp forms the reflector of
+  //         column j itself (the same reduction in the same order, so the same tau and scale in
+  //         every warp) instead of waiting for one warp to broadcast it, and reads the reflector
+  //         straight from column j; after p = tau A22 v each row's owner stores the reflector's
+  //         entry in column j (kept for the back-transformation) as it updates the row.
   for (int j = 0; j + 2 < m; ++j) {
     const int sN = m - j - 1;
-    if (wid == 0) {
-      float x0 = A[(j + 1) * kTriLd + j];
-      float acc = 0.f;
-      for (int k = 1 + lane; k < sN; k += 32) {
-        float x = A[(j + 1 + k) * kTriLd + j];
-        acc = fmaf(x, x, acc);
-      }
-      acc = warp_sum_f(acc);
-      if (lane == 0) {
-        if (acc == 0.f) {
-          sh_tau = 0.f; sh_scale = 0.f; ev[j] = x0;
-        } else {
-          float nrm = sqrtf(x0 * x0 + acc);
-          float beta = (x0 >= 0.f) ? -nrm : nrm;
-          sh_tau = (beta - x0) / beta;
-          sh_scale = 1.f / (x0 - beta);
-          ev[j] = beta;
-        }
-        dv[j] = A[j * kTriLd + j];
-        tauv[j] = sh_tau;
-      }
+    const float x0 = A[(j + 1) * kTriLd + j];
+    float nacc = 0.f;
+    for (int k = 1 + lane; k < sN; k += 32) {
+      const float x = A[(j + 1 + k) * kTriLd + j];
+      nacc = fmaf(x, x, nacc);
     }
-    __syncthreads();
-    const float tau = sh_tau, scale = sh_scale;
-    for (int k = tid; k < sN; k += blockDim.x) {
-      float v = (tau == 0.f) ? ((k == 0) ? 1.f : 0.f)
-                             : ((k == 0) ? 1.f : A[(j + 1 + k) * kTriLd + j] * scale);
-      vb[k] = v;
-      A[(j + 1 + k) * kTriLd + j] = v;  // the reflector, kept below the diagonal
+    nacc = warp_sum_f(nacc);
+    float tau = 0.f, scale = 0.f, beta = x0;
+    if (nacc != 0.f) {
+      const float nrm = sqrtf(x0 * x0 + nacc);
+      beta = (x0 >= 0.f) ? -nrm : nrm;
+      tau = (beta - x0) / beta;
+      scale = 1.f / (x0 - beta);
     }
-    __syncthreads();
+    if (tid == 0) {
+      ev[j] = beta;
+      dv[j] = A[j * kTriLd + j];
+      tauv[j] = tau;
+    }
     if (tau != 0.f) {
       float vreg[4], preg[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        int c = lane + 32 * q;
-        vreg[q] = (c < sN) ? vb[c] : 0.f;
+        const int c = lane + 32 * q;
+        vreg[q] = (c < sN) ? ((c == 0) ? 1.f : A[(j + 1 + c) * kTriLd + j] * scale) : 0.f;
       }
       // p = tau * A22 v, one warp per row, four rows per warp reduced together
       for (int rb = wid; rb < sN; rb += 4 * nw) {
@@ -532,7 +524,7 @@ __global__ void __launch_bounds__(kJacThreads, 1) k_eig_tri(Geom g, Bufs b) {
             if (rb + u * nw < sN) pv[rb + u * nw] = tau * acc[u];
         }
       }
-      __syncthreads();
+      __syncthreads();  // pv complete; every warp has read column j
       float acc = 0.f;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -544,16 +536,21 @@ __global__ void __launch_bounds__(kJacThreads, 1) k_eig_tri(Geom g, Bufs b) {
       float wreg[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) wreg[q] = preg[q] - K * vreg[q];
-      // A22 -= v w^T + w v^T
+      // A22 -= v w^T + w v^T; the reflector entry of the row goes to column j
       for (int r = wid; r < sN; r += nw) {
-        const float vr = vb[r], wr = pv[r] - K * vr;
-        float* arow = A + (j + 1 + r) * kTriLd + (j + 1);
+        float* cj = A + (j + 1 + r) * kTriLd + j;
+        const float vr = (r == 0) ? 1.f : cj[0] * scale, wr = pv[r] - K * vr;
+        float* arow = cj + 1;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           int c = lane + 32 * q;
           if (c < sN) arow[c] = arow[c] - vr * wreg[q] - wr * vreg[q];
         }
+        __syncwarp();
+        if (lane == 0) cj[0] = vr;
       }
+    } else {
+      for (int k = tid; k < sN; k += blockDim.x) A[(j + 1 + k) * kTriLd + j] = (k == 0) ? 1.f : 0.f;
     }
     __syncthreads();
   }
@@ -706,33 +703,33 @@ __global__ void __launch_bounds__(kJacThreads, 1) k_eig_tri(Geom g, Bufs b) {
   }
   __syncthreads();
   PHASE_MARK(tph, "tri.complement");
-  // ---- d. back-transformation Z <- H_0 ... H_{m-3} Z: eight threads per column, each with
-  //         16 consecutive rows of its column in registers
+  // ---- d. back-transformation Z <- H_0 ... H_{m-3} Z: eight threads per column, thread gl of
+  //         a column holding rows gl, gl + 8, ..., gl + 120 of it in registers. With this
+  //         interleaving the eight threads read eight consecutive rows of a reflector (stored in
+  //         column j of A, row stride kTriLd = 1 mod 32 banks) in one conflict-free access; with
+  //         16 consecutive rows per thread the same reads hit 4-way bank conflicts.
   {
     const int G = 8;
     const int col = tid / G, gl = tid % G;
     const unsigned gmask = 0xffu << ((lane / G) * G);
-    const int r0 = gl * 16;
     float z[16];
     if (col < m) {
 #pragma unroll
-      for (int k = 0; k < 16; ++k) z[k] = (r0 + k < m) ? Z[(r0 + k) * kTriLd + col] : 0.f;
+      for (int k = 0; k < 16; ++k) {
+        const int r = gl + G * k;
+        z[k] = (r < m) ? Z[r * kTriLd + col] : 0.f;
+      }
     }
     for (int j = m - 3; j >= 0; --j) {
       const float tau = tauv[j];
       if (tau == 0.f) continue;
       float a[16];
       float acc = 0.f;
-      if (r0 + 15 > j) {
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          const int r = r0 + k;
-          a[k] = (r > j && r < m) ? A[r * kTriLd + j] : 0.f;
-          acc = fmaf(a[k], z[k], acc);
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < 16; ++k) a[k] = 0.f;
+      for (int k = 0; k < 16; ++k) {
+        const int r = gl + G * k;
+        a[k] = (r > j && r < m) ? A[r * kTriLd + j] : 0.f;
+        acc = fmaf(a[k], z[k], acc);
       }
       for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(gmask, acc, o);
       acc *= tau;
@@ -741,8 +738,10 @@ __global__ void __launch_bounds__(kJacThreads, 1) k_eig_tri(Geom g, Bufs b) {
     }
     if (col < m) {
 #pragma unroll
-      for (int k = 0; k < 16; ++k)
-        if (r0 + k < m) Z[(r0 + k) * kTriLd + col] = z[k];
+      for (int k = 0; k < 16; ++k) {
+        const int r = gl + G * k;
+        if (r < m) Z[r * kTriLd + col] = z[k];
+      }
     }
   }
   __syncthreads();
