@@ -524,7 +524,7 @@ def run_ours(a, rank, world):
                 "frac": achieved / peak, "traffic": traffic,
                 "traffic_source": DENSE_TRAFFIC_SOURCE if traffic is not None else None,
                 "kernel": f"k_dense_tma<{p.ranks[-1]},0,{int(p.dims[-1] <= 2048)}>", "ms_per_launch": dms,
-                "peak_source": f"{src} (burst copy bandwidth); the >= 0.70 target is judged on it",
+                "peak_source": f"{src} (burst copy bandwidth); the >= 0.70 target refers to it",
                 "frac_of_nominal": achieved / NOMINAL_HBM_GBS, "nominal_peak": NOMINAL_HBM_GBS,
                 "iteration_frac": alg_bytes / (ms / K / 1e3) / 1e9 / peak,
                 "algorithmic_bytes_per_launch": alg_bytes}
