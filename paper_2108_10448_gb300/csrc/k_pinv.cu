@@ -944,21 +944,34 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
   if (tid == 0) tie = 0;
   // the FP32 eigenbasis and its top-r columns: the cold path only (the warm attempt runs before
   // the eigensolver of this iteration)
-  if (mode == 1 && tid == 0) {
-    for (int a = 0; a < m; ++a) pos_of[a] = -1;
-    for (int j = 0; j < r; ++j) {  // r largest eigenvalues, descending; ties broken by index
-      int best = -1;
-      for (int a = 0; a < m; ++a)
-        if (pos_of[a] < 0 && (best < 0 || lam[a] > lam[best])) best = a;
-      top[j] = best;
-      pos_of[best] = j;
+  if (mode == 1 && wid == 0) {
+    // the r largest eigenvalues, descending, ties broken by the lower index: each round takes
+    // the warp's (largest value, lowest index) among the indices not yet taken
+    for (int a = lane; a < m; a += 32) pos_of[a] = -1;
+    __syncwarp();
+    for (int j = 0; j < r; ++j) {
+      float bv = 0.f;
+      int bi = -1;
+      for (int a = lane; a < m; a += 32)
+        if (pos_of[a] < 0 && (bi < 0 || lam[a] > bv)) { bv = lam[a]; bi = a; }
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (oi >= 0 && (bi < 0 || ov > bv || (ov == bv && oi < bi))) { bv = ov; bi = oi; }
+      }
+      if (lane == 0) {
+        top[j] = bi;
+        pos_of[bi] = j;
+      }
+      __syncwarp();
     }
-    if (mode == 1 && crank == 0) {  // the gate for the next warm attempt, from this spectrum
+    if (crank == 0) {  // the gate for the next warm attempt, from this spectrum
       double t2 = 0.0;
-      for (int a = 0; a < m; ++a)
+      for (int a = lane; a < m; a += 32)
         if (pos_of[a] < 0) t2 += (double)lam[a] * (double)lam[a];
+      t2 = warp_sum_d(t2);
       const double lr = (double)lam[top[r - 1]];
-      b.wratio[i] = (lr > 0.0) ? sqrt(t2) / lr : 1e30;
+      if (lane == 0) b.wratio[i] = (lr > 0.0) ? sqrt(t2) / lr : 1e30;
     }
   }
   for (int t = tid; t < own * m; t += blockDim.x) {
