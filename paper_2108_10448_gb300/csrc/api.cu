@@ -44,8 +44,8 @@ struct rtcur_plan {
   float* S_internal = nullptr;
   float* S_work = nullptr;
   const float* X = nullptr;
-  cudaStream_t cap = nullptr, side = nullptr;
-  cudaEvent_t evFork = nullptr, evJoin = nullptr;
+  cudaStream_t cap = nullptr, side = nullptr, side2 = nullptr;
+  cudaEvent_t evFork = nullptr, evJoin = nullptr, evFork2 = nullptr, evJoin2 = nullptr;
   cudaGraph_t loopG = nullptr, iterG = nullptr;
   cudaGraphExec_t loopX = nullptr, iterX = nullptr;
   BwWork bw;             // adjoint workspace (options.checkpoint > 0)
@@ -105,8 +105,14 @@ cudaError_t capture_body(rtcur_plan* p, cudaStream_t s, unsigned long long handl
   if ((e = launch_refine(g, b, 0, s)) != cudaSuccess) return e;  // warm attempt
   if ((e = launch_jacobi(g, b, s)) != cudaSuccess) return e;
   if ((e = launch_refine(g, b, 1, s)) != cudaSuccess) return e;
-  if ((e = launch_factor_B(g, b, s)) != cudaSuccess) return e;
+  // B_i = C_i Y_i and the core G = R x_i Q_i^T read disjoint inputs and write disjoint buffers:
+  // two branches of the graph, joined before the table that needs both
+  if ((e = cudaEventRecord(p->evFork2, s)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(p->side2, p->evFork2, 0)) != cudaSuccess) return e;
+  if ((e = launch_factor_B(g, b, p->side2)) != cudaSuccess) return e;
+  if ((e = cudaEventRecord(p->evJoin2, p->side2)) != cudaSuccess) return e;
   if ((e = launch_core(g, b, s)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(s, p->evJoin2, 0)) != cudaSuccess) return e;
   if ((e = launch_table(g, b, 1, s)) != cudaSuccess) return e;
   if (full && p->opt.dense_form == RTCUR_FORM_FP32_PLAIN && (e = launch_plain_prep(g, b, s)) != cudaSuccess) return e;
   if ((e = launch_sample_err(g, b, s)) != cudaSuccess) return e;
@@ -519,8 +525,11 @@ rtcur_status rtcur_create(rtcur_plan** out, int32_t n_modes, const int64_t* dims
   if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
   if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&p->cap, cudaStreamNonBlocking, prio_hi);
   if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&p->side, cudaStreamNonBlocking, prio_lo);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&p->side2, cudaStreamNonBlocking, prio_hi);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->evFork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->evJoin, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->evFork2, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->evJoin2, cudaEventDisableTiming);
   if (e == cudaSuccess) {
     size_t sm = jacobi_smem_bytes(mx);
     e = prepare_jacobi(sm);
@@ -863,8 +872,11 @@ void rtcur_destroy(rtcur_plan* p) {
   if (p->iterG) cudaGraphDestroy(p->iterG);
   if (p->evFork) cudaEventDestroy(p->evFork);
   if (p->evJoin) cudaEventDestroy(p->evJoin);
+  if (p->evFork2) cudaEventDestroy(p->evFork2);
+  if (p->evJoin2) cudaEventDestroy(p->evJoin2);
   if (p->cap) cudaStreamDestroy(p->cap);
   if (p->side) cudaStreamDestroy(p->side);
+  if (p->side2) cudaStreamDestroy(p->side2);
   for (void* v : p->allocs) cudaFree(v);
   delete p;
 }
