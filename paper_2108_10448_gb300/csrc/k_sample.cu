@@ -18,6 +18,10 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kHtBlocksFull = 2 * 152;
+// Alone (SAMPLED scope) the threshold and error kernels run one wave of three blocks per SM, each
+// thread looping over more entries: 1024 blocks (two waves of the four that fit an SM) took
+// 5.6% longer per solve at 800^3, 608 blocks 1%.
+constexpr int kHtBlocksSampled = 3 * 152;
 constexpr int kMaxRedBlocks = 1024;
 
 // X at flat index `idx` as the sampled step reads it: the caller's FP32 tensor, or its BF16 copy
@@ -32,22 +36,10 @@ __device__ __forceinline__ const long long* current_set(const Geom& g, const Buf
   return b.idx + s * g.set_len;
 }
 
-// Block-wide sum of `v` (kThreads threads); result valid in thread 0.
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) sh[w] = v;
-  __syncthreads();
-  double t = 0.0;
-  if (threadIdx.x == 0)
-    for (int i = 0; i < kThreads / 32; ++i) t += sh[i];
-  return t;
-}
-
-// Block-wide sums of N values at once (kThreads threads): the same shuffle tree and the same
-// warp order as block_sum, so each sum is bit-identical to N separate block_sum calls, but with one
-// barrier instead of 2N. Sum j is returned in thread j (j < N).
+// Block-wide sums of N values at once (kThreads threads): each value is summed by a shuffle-down
+// tree within every warp, then over the warps in order, all N sums sharing one barrier (instead
+// of two per sum when summed one at a time; the order of every sum is the same). Sum j is
+// returned in thread j (j < N).
 template <int N>
 __device__ __forceinline__ double block_sum_n(const double (&v)[N], double* sh) {
   double r[N];
@@ -80,14 +72,6 @@ __device__ __forceinline__ double sum_partials_n(const double* part, int nb, dou
 #pragma unroll
     for (int j = 0; j < N; ++j) acc[j] += part[i * RT_RED_SLOTS + j];
   return block_sum_n<N>(acc, sh);
-}
-
-// Sum of slot `slot` over the first `nb` block partials, by the whole block (fixed order per
-// thread, then a block sum); result valid in thread 0.
-__device__ __forceinline__ double sum_partials(const double* part, int nb, int slot, double* sh) {
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += part[i * RT_RED_SLOTS + slot];
-  return block_sum(acc, sh);
 }
 
 __global__ void k_setup(Geom g, Bufs b, double zeta0) {
@@ -413,7 +397,8 @@ cudaError_t launch_sample_ht(const Geom& g, const Bufs& b, cudaStream_t s) {
   // per SM of 256 threads x 64 registers) leave every SM room for one of its persistent CTAs,
   // which would otherwise wait for this kernel's blocks to drain (~30 us per iteration).
   int grid = grid_for(g.nS);
-  if (g.scope == RTCUR_SCOPE_FULL && grid > kHtBlocksFull) grid = kHtBlocksFull;
+  const int cap = (g.scope == RTCUR_SCOPE_FULL) ? kHtBlocksFull : kHtBlocksSampled;
+  if (grid > cap) grid = cap;
   k_sample_ht<<<grid, kThreads, 0, s>>>(g, b);
   return cudaGetLastError();
 }
@@ -423,7 +408,8 @@ cudaError_t launch_sample_err(const Geom& g, const Bufs& b, cudaStream_t s) {
   // threshold kernel, take fewer of the pass's issue slots (measured 1.5% faster iterations at
   // 800^3 than 1024 blocks; one block per SM for both kernels lengthens the chain instead).
   int grid = grid_for(g.nS);
-  if (g.scope == RTCUR_SCOPE_FULL && grid > kHtBlocksFull) grid = kHtBlocksFull;
+  const int cap = (g.scope == RTCUR_SCOPE_FULL) ? kHtBlocksFull : kHtBlocksSampled;
+  if (grid > cap) grid = cap;
   k_sample_err<<<grid, kThreads, 0, s>>>(g, b);
   return cudaGetLastError();
 }
