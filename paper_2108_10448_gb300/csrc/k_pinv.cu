@@ -842,6 +842,43 @@ __device__ __forceinline__ double quad_sum_d(double v) {
   return v;
 }
 
+// C = A^T B for the m x r panels A, B (row-major, row stride r, shared memory), FP64: entry
+// (j, l) is one dot product over a half warp (terms a = lane mod 16), so each warp forms two
+// entries at a time and the chain of an entry is m / 16 FMAs and four shuffle-adds. The loop is
+// uniform over the block (every lane takes part in every shuffle). sym (A = B): only l <= j is
+// formed, and mirrored. The caller synchronises before C is read.
+__device__ __forceinline__ void panel_atb(const double* A, const double* B, int m, int r, bool sym,
+                                          double* C) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int h = lane >> 4, hl = lane & 15;
+  const int ne = sym ? r * (r + 1) / 2 : r * r;
+  for (int base = 0; base < ne; base += 2 * nw) {
+    const int t = base + 2 * wid + h;
+    const bool act = t < ne;
+    int j = 0, l = 0;
+    if (act) {
+      if (sym) {
+        while ((j + 1) * (j + 2) / 2 <= t) ++j;
+        l = t - j * (j + 1) / 2;
+      } else {
+        j = t / r;
+        l = t - j * r;
+      }
+    }
+    double acc = 0.0;
+    if (act)
+      for (int a = hl; a < m; a += 16) acc = fma(A[a * r + j], B[a * r + l], acc);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 8);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    if (act && hl == 0) {
+      C[j * r + l] = acc;
+      if (sym) C[l * r + j] = acc;
+    }
+  }
+}
+
 __device__ __forceinline__ void load_panel(double* dst, const double* src, int n) {
   for (int t = threadIdx.x; t < n; t += blockDim.x) dst[t] = src[t];
 }
@@ -1017,13 +1054,7 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
       if (act && ql == 0) sYb[(lo + a) * r + j] = acc;
     }
     exchange_panel(sYb, m, r, crank, rown);
-    for (int t = wid; t < r * r; t += nw) {
-      int j = t / r, l = t % r;
-      double acc = 0.0;
-      for (int a = lane; a < m; a += 32) acc = fma(sYb[a * r + j], sYb[a * r + l], acc);
-      acc = warp_sum_d(acc);
-      if (lane == 0) Gq[t] = acc;
-    }
+    panel_atb(sYb, sYb, m, r, true, Gq);
     __syncthreads();
     if (tid == 0) {
       chol_ok = chol_small(Gq, r, invd) ? 1 : 0;
@@ -1220,13 +1251,7 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
     if (act && ql == 0) sYw[(lo + a) * r + j] = acc;
   }
   exchange_panel(sYw, m, r, crank, rown);
-  for (int t = wid; t < r * r; t += nw) {
-    int j = t / r, l = t % r;
-    double acc = 0.0;
-    for (int a = lane; a < m; a += 32) acc = fma(sX1[a * r + j], sYw[a * r + l], acc);
-    acc = warp_sum_d(acc);
-    if (lane == 0) Hs[t] = acc;
-  }
+  panel_atb(sX1, sYw, m, r, false, Hs);
   __syncthreads();
   __shared__ int fast_ok;
   __shared__ double cert[3];
@@ -1430,13 +1455,7 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
   }
   // ---- exact path (H close to the SVD_r cutoff): singular vectors and the cutoff
   // F1: orthonormalise X1 (Cholesky QR in FP64)
-  for (int t = wid; t < r * r; t += nw) {
-    int j = t / r, l = t % r;
-    double acc = 0.0;
-    for (int a = lane; a < m; a += 32) acc = fma(sX1[a * r + j], sX1[a * r + l], acc);
-    acc = warp_sum_d(acc);
-    if (lane == 0) Gq[t] = acc;
-  }
+  panel_atb(sX1, sX1, m, r, true, Gq);
   __syncthreads();
   if (tid == 0) {  // Gq <- L (lower Cholesky factor), in place
     for (int j = 0; j < r; ++j) {
@@ -1485,13 +1504,7 @@ __global__ void __launch_bounds__(kRefThreads) k_refine(Geom g, Bufs b, int mode
   exchange_panel(sYw, m, r, crank, rown);
   PHASE_MARK(tph, "ref.qr+MQ");
   // F3: H = Q^T M Q (r x r), its eigenpairs by FP64 cyclic Jacobi, cutoff of SVD_r
-  for (int t = wid; t < r * r; t += nw) {
-    int j = t / r, l = t % r;
-    double acc = 0.0;
-    for (int a = lane; a < m; a += 32) acc = fma(sX1[a * r + j], sYw[a * r + l], acc);
-    acc = warp_sum_d(acc);
-    if (lane == 0) Hs[t] = acc;
-  }
+  panel_atb(sX1, sYw, m, r, false, Hs);
   __syncthreads();
   if (tid == 0) {
     for (int j = 0; j < r; ++j) {  // symmetrise, identity start
