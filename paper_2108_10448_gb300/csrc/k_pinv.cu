@@ -2,21 +2,30 @@
 // W_i = C_i(I_i, :), an m_i x q_i matrix), computed in FP64 as the top-r_i eigenpairs of the
 // Gram matrix M_i = W_i W_i^T:  W_r^+ = V_r Sigma_r^-1 Q_r^T with V_r Sigma_r = W^T Q_r.
 //
-// GB300 runs FP64 at 1/58 of its FP32 rate, so the FP64 work is kept GEMM-shaped and spread
-// over many SMs, and the sequential part runs in FP32:
-//   1. k_gram    M_i in FP64 (FP32 products are exact in FP64), 8x8 output tiles over the grid.
-//   2. k_jacobi  FP32 cyclic Jacobi on fl32(M_i), round-robin pair ordering (parallel Jacobi,
-//                Brent and Luk 1985), one CTA per mode, matrix and vectors in shared memory.
-//                Gives an FP32-accurate full eigenbasis Xh and eigenvalues lam.
-//   3. k_refine  FP64 refinement of the top-r subspace by the Ogita-Aishima iteration
-//                (Ogita and Aishima 2018, "Iterative refinement for symmetric eigenvalue
-//                decomposition"), restricted to the top block against the tail (pairs inside the
-//                top block or inside the tail are not rotated; their first-order term is the
-//                orthogonality correction only). Each step roughly squares the subspace error;
-//                two steps take the FP32 basis to FP64 accuracy. Then an FP64 Rayleigh-Ritz on
-//                the r x r block, the cutoff of SVD_r, and Y_i = V_r Sigma_r^-1 = W^T Q_r
-//                Sigma_r^-2. One thread-block cluster of 16 (or 8) CTAs per mode shares the
-//                m x r panels through global memory (L2) between cluster barriers.
+// GB300 runs FP64 at a small fraction of its FP32 rate, so the FP64 work is kept to dot
+// products spread over many lanes and SMs, and the sequential eigensolver runs in FP32:
+//   1. k_gram    M_i in FP64 (FP32 products are exact in FP64), 8x8 output tiles over the grid,
+//                each dot product split over a quad of lanes.
+//   2. k_refine, mode 0 (warm attempt, iterations k >= 1): FP64 subspace iteration with Cholesky
+//                QR from the previous iteration's basis (RTCUR-F) or the current factor's rows on
+//                the new index set (RTCUR-R), accepted only with a certificate that separates the
+//                top-r eigenvalues from the rest and bounds the basis error (below); then the
+//                fast finish. When it succeeds for a mode, steps 3 and 4 do nothing for it.
+//   3. k_eig_tri FP32 eigenbasis of fl32(M_i): Householder tridiagonalisation, multisection on
+//                Sturm counts, twisted-factorisation eigenvectors, back-transformation; one CTA
+//                per mode (k_jacobi, a round-robin parallel Jacobi, is the alternative option).
+//   4. k_refine, mode 1 (cold path): FP64 refinement of the top-r subspace by the Ogita-Aishima
+//                iteration (Ogita and Aishima 2018, "Iterative refinement for symmetric
+//                eigenvalue decomposition"), restricted to the top block against the tail (pairs
+//                inside the top block or inside the tail are not rotated; their first-order term
+//                is the orthogonality correction only). Each step roughly squares the subspace
+//                error; two steps take the FP32 basis to FP64 accuracy. Then the fast finish
+//                (L needs only the top-r invariant subspace: one r x r Cholesky) or, near the
+//                SVD_r cutoff, an FP64 Rayleigh-Ritz on the r x r block with the cutoff, and
+//                Y_i = V_r Sigma_r^-1 = W^T Q_r Sigma_r^-2.
+// k_refine runs one thread-block cluster of 16 (or 8, 4, 2) CTAs per mode; each CTA owns rows of
+// the m x r panels and reads the others' rows from their shared memory (distributed shared
+// memory) after a cluster barrier.
 #include <cooperative_groups.h>
 
 #include "rtcur_internal.cuh"
